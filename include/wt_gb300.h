@@ -1,0 +1,173 @@
+/*
+ * wt_gb300 -- bottom-up wavelet tree / wavelet matrix construction on GB300.
+ *
+ * Method: Fischer, Kurpicz, Loebel, "Simple, Fast and Lightweight Parallel
+ * Wavelet Tree Construction" (arXiv:1702.07578), prefix counting (Alg. 1 and
+ * Alg. 2, Sec. 3; wavelet matrix adaption, Sec. 5.1).
+ *
+ * Problem (Sec. 2): a text T[0, n) over the alphabet [0, sigma) is turned into
+ * L = ceil(lg sigma) bit vectors BV_0 .. BV_{L-1} of n bits each.  Level l of
+ * the wavelet tree (WT) holds bit l (counted from the most significant of the
+ * L code bits) of the symbols stably sorted by their l-bit prefix (Obs. 1).
+ * Level l of the wavelet matrix (WM) holds bit l of the symbols stably sorted
+ * by their reversed l-bit prefix (Obs. 2), and Z[l] is its number of zeros.
+ * Only the bit vectors are built; rank/select support is not (Sec. 4).
+ *
+ * Output layout (the paper does not fix the bit order inside a word): level l
+ * occupies 64-bit words [l*W, (l+1)*W) of d_bv with W = wt_words_per_level(n);
+ * bit j of a level is bit (j & 63) of word (j >> 6), least significant first;
+ * bits >= n of the last word are written as zero.  d_zeros receives L values.
+ *
+ * Memory: every pointer named d_* is device memory owned by the caller.  The
+ * library allocates nothing in the build calls; it uses the caller's
+ * workspace (size from the *_workspace_size calls, any alignment >= 256 B).
+ * Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
+ * void*, NULL = legacy default stream).  A workspace must not be shared by
+ * two builds in flight.
+ *
+ * Errors: argument errors are returned at once and nothing is launched.
+ * Errors found on the device (a symbol >= sigma) are recorded in the
+ * workspace; wt_sync_status() synchronises the stream and returns them.
+ * After a device-detected error the contents of d_bv / d_zeros are
+ * unspecified (the kernels still write only inside the caller's buffers).
+ * No call aborts the process.
+ *
+ * Limits: n < 2^40 per text; sigma <= 2^32 for the WM; sigma <= 2^24 for
+ * the WT (larger alphabets return WT_ERR_INVALID_ARG).  The storage type
+ * must hold sigma - 1 (sigma <= 2^8 for WT_U8, <= 2^16 for WT_U16).
+ */
+#ifndef WT_GB300_H
+#define WT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WT_OK = 0,
+    WT_ERR_INVALID_ARG = 1,    /* bad pointer, size, type or alphabet      */
+    WT_ERR_SYMBOL_RANGE = 2,   /* device found a symbol >= sigma           */
+    WT_ERR_OUT_OF_MEMORY = 3,  /* workspace too small / allocation failed  */
+    WT_ERR_CUDA = 4,           /* a CUDA runtime call failed               */
+    WT_ERR_TIMEOUT = 5,        /* a bounded wait ran out                   */
+    WT_ERR_BUSY = 6,           /* server: request cannot be admitted now   */
+    WT_ERR_NOT_FOUND = 7       /* server: unknown or released ticket       */
+} wt_status;
+
+typedef enum { WT_U8 = 1, WT_U16 = 2, WT_U32 = 4 } wt_symtype;   /* bytes per symbol */
+typedef enum { WT_TREE = 0, WT_MATRIX = 1 } wt_kind;
+
+/* L = ceil(lg sigma), the number of levels (Sec. 2); 0 when sigma <= 1. */
+uint32_t wt_levels(uint64_t sigma);
+
+/* W = ceil(n / 64), the 64-bit words of one level. */
+uint64_t wt_words_per_level(uint64_t n);
+
+/* Human-readable name of a status code (static storage). */
+const char *wt_status_string(wt_status s);
+
+/* Workspace bytes needed by wt_build (kind = WT_TREE) or wm_build
+ * (kind = WT_MATRIX) for one text of n symbols over [0, sigma). */
+wt_status wt_workspace_size(wt_kind kind, wt_symtype type, uint64_t n, uint64_t sigma,
+                            size_t *bytes);
+
+/* Wavelet tree of one text (Alg. 1 / Alg. 2 with id = identity, Sec. 3).
+ *   d_text  n symbols of the given storage type, each < sigma
+ *   d_bv    L * W words, written completely (see layout above)
+ *   d_ws    workspace of ws_bytes >= wt_workspace_size(WT_TREE, ...)
+ * n = 0 or sigma = 1 is valid and writes nothing. */
+wt_status wt_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                   uint64_t *d_bv, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Wavelet matrix of one text (Sec. 5.1: id replaced by the bit-reversal
+ * permutation).  d_zeros receives Z[0..L) (Sec. 5, number of zeros of each
+ * level); it may be NULL when L = 0. */
+wt_status wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                   uint64_t *d_bv, uint64_t *d_zeros, void *d_ws, size_t ws_bytes,
+                   void *stream);
+
+/* Synchronise the stream and return the first error the device recorded in
+ * this workspace during the last build on it (WT_OK if none), then clear it. */
+wt_status wt_sync_status(void *d_ws, void *stream);
+
+/* ---- batched construction ---------------------------------------------
+ * Many independent texts built together (all WT or all WM, one storage
+ * type).  Each descriptor names its device text, length, alphabet and
+ * output buffers (d_zeros only for WT_MATRIX).  The descriptors are read
+ * from host memory during the call and may be reused after it returns.
+ * Output is bit-identical to one wt_build / wm_build per text. */
+typedef struct {
+    const void *d_text;
+    uint64_t n;
+    uint64_t sigma;
+    uint64_t *d_bv;
+    uint64_t *d_zeros;
+} wt_text_desc;
+
+wt_status wt_batched_workspace_size(wt_kind kind, wt_symtype type, const wt_text_desc *h_descs,
+                                    uint32_t count, size_t *bytes);
+
+wt_status wt_build_batched(wt_kind kind, wt_symtype type, const wt_text_desc *h_descs,
+                           uint32_t count, void *d_ws, size_t ws_bytes, void *stream);
+
+/* ---- serving -------------------------------------------------------------
+ * A server owns device memory (bounded by hbm_budget_bytes) and a set of
+ * CUDA streams on one device.  Requests (host texts) are admitted while
+ * their footprint (text + output + workspace) fits in the budget, batched
+ * as they arrive, built concurrently on the streams, and kept resident on
+ * the device until released.  All server calls are thread-safe. */
+typedef struct wt_server wt_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;   /* device memory the server may hold            */
+    uint32_t max_batch;        /* requests per batch launch (>= 1)             */
+    uint32_t streams;          /* concurrent CUDA streams (>= 1)               */
+    int device;                /* CUDA device ordinal                          */
+    uint32_t max_pending;      /* queued requests before submit returns BUSY   */
+} wt_server_config;
+
+typedef struct {
+    wt_kind kind;
+    wt_symtype type;
+    const void *h_text;        /* host text; copied during submit              */
+    uint64_t n;
+    uint64_t sigma;
+} wt_request;
+
+typedef struct {
+    const uint64_t *d_bv;      /* L * W words, device, valid until release     */
+    const uint64_t *d_zeros;   /* L values for WT_MATRIX, else NULL            */
+    uint32_t levels;
+    uint64_t words_per_level;
+    uint64_t n;
+    wt_status status;          /* build status of this request                 */
+    double latency_us;         /* submit -> completion                         */
+} wt_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, in_flight;
+    double p50_us, p99_us;     /* latency over completed requests              */
+    double symbols_per_s;      /* completed symbols / wall time since create   */
+    size_t hbm_in_use;
+} wt_server_stats;
+
+wt_status wt_server_create(const wt_server_config *cfg, wt_server **out);
+/* Copy the request's text and queue it; WT_ERR_BUSY if the queue is full or
+ * the request alone exceeds the budget.  *ticket identifies it. */
+wt_status wt_server_submit(wt_server *s, const wt_request *req, uint64_t *ticket);
+/* Wait until the request is built (timeout_us < 0: no limit); WT_ERR_TIMEOUT
+ * if the limit passes first. */
+wt_status wt_server_wait(wt_server *s, uint64_t ticket, int64_t timeout_us, wt_result *res);
+/* Free the request's device memory; the ticket becomes invalid. */
+wt_status wt_server_release(wt_server *s, uint64_t ticket);
+wt_status wt_server_get_stats(wt_server *s, wt_server_stats *st);
+/* Finish in-flight work, free everything. */
+void wt_server_destroy(wt_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WT_GB300_H */

@@ -1,0 +1,172 @@
+"""Python binding of ``libwt_gb300`` (bottom-up wavelet tree / matrix construction).
+
+Same names as the C ABI in ``include/wt_gb300.h``; these functions only marshal
+arguments: PyTorch supplies device memory and streams, every step of the
+construction runs in the library's CUDA kernels.  There is no CPU path: if the
+library cannot be built or loaded, every call raises.
+
+Bit vectors come back as int64 tensors of shape (L, ceil(n/64)) holding the
+uint64 words (bit j of a level is bit j & 63 of word j >> 6).
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _native
+
+WT_TREE, WT_MATRIX = 0, 1
+WT_U8, WT_U16, WT_U32 = 1, 2, 4
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "symbol out of range", 3: "out of memory",
+          4: "CUDA error", 5: "timeout", 6: "busy", 7: "not found"}
+
+
+class WtError(RuntimeError):
+    def __init__(self, code, where=""):
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+def _check(code, where):
+    if code != 0:
+        raise WtError(code, where)
+
+
+def build():
+    """Compile the CUDA library (sm_103a) in-tree."""
+    return _native.build()
+
+
+def lib():
+    return _native.lib()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _symtype(t):
+    torch = _torch()
+    m = {torch.uint8: WT_U8, torch.int16: WT_U16, torch.int32: WT_U32}
+    if hasattr(torch, "uint16"):
+        m[torch.uint16] = WT_U16
+    if hasattr(torch, "uint32"):
+        m[torch.uint32] = WT_U32
+    if t.dtype not in m:
+        raise TypeError(f"unsupported text dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def wt_levels(sigma: int) -> int:
+    return int(lib().wt_levels(int(sigma)))
+
+
+def wt_words_per_level(n: int) -> int:
+    return int(lib().wt_words_per_level(int(n)))
+
+
+def wt_status_string(code: int) -> str:
+    return lib().wt_status_string(int(code)).decode()
+
+
+def wt_workspace_size(kind: int, symtype: int, n: int, sigma: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().wt_workspace_size(kind, symtype, int(n), int(sigma), ctypes.byref(out)),
+           "wt_workspace_size")
+    return out.value
+
+
+def _alloc(text, sigma, bv, zeros, ws, kind):
+    torch = _torch()
+    n = text.numel()
+    L = wt_levels(sigma)
+    W = wt_words_per_level(n)
+    dev = text.device
+    if bv is None:
+        bv = torch.empty((L, W), dtype=torch.int64, device=dev)
+    if kind == WT_MATRIX and zeros is None:
+        zeros = torch.empty((max(L, 1),), dtype=torch.int64, device=dev)
+    if ws is None:
+        ws = torch.empty((max(wt_workspace_size(kind, _symtype(text), n, sigma), 1),),
+                         dtype=torch.uint8, device=dev)
+    return bv, zeros, ws
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else 0)
+
+
+def wt_build(text, sigma: int, bv=None, ws=None, stream=None):
+    """Wavelet tree of a device text; returns the (L, W) int64 bit-vector tensor."""
+    if not text.is_cuda or not text.is_contiguous():
+        raise ValueError("text must be a contiguous CUDA tensor")
+    bv, _, ws = _alloc(text, sigma, bv, None, ws, WT_TREE)
+    _check(lib().wt_build(_ptr(text), _symtype(text), text.numel(), int(sigma), _ptr(bv), _ptr(ws),
+                          ws.numel(), _stream(stream)), "wt_build")
+    return bv
+
+
+def wm_build(text, sigma: int, bv=None, zeros=None, ws=None, stream=None):
+    """Wavelet matrix of a device text; returns (bit vectors, Z)."""
+    if not text.is_cuda or not text.is_contiguous():
+        raise ValueError("text must be a contiguous CUDA tensor")
+    bv, zeros, ws = _alloc(text, sigma, bv, zeros, ws, WT_MATRIX)
+    _check(lib().wm_build(_ptr(text), _symtype(text), text.numel(), int(sigma), _ptr(bv),
+                          _ptr(zeros), _ptr(ws), ws.numel(), _stream(stream)), "wm_build")
+    return bv, zeros[:wt_levels(sigma)]
+
+
+def wt_sync_status(ws, stream=None):
+    """Synchronise and raise WtError if the device recorded an error in ws."""
+    _check(lib().wt_sync_status(_ptr(ws), _stream(stream)), "device")
+
+
+def _descs(texts, sigmas, bvs, zeros):
+    arr = (_native.WtTextDesc * len(texts))()
+    for i, t in enumerate(texts):
+        arr[i].d_text = t.data_ptr() if t.numel() else 0
+        arr[i].n = t.numel()
+        arr[i].sigma = int(sigmas[i])
+        arr[i].d_bv = bvs[i].data_ptr() if bvs is not None and bvs[i].numel() else 0
+        arr[i].d_zeros = zeros[i].data_ptr() if zeros is not None and zeros[i].numel() else 0
+    return arr
+
+
+def wt_batched_workspace_size(kind: int, symtype: int, lengths, sigmas) -> int:
+    arr = (_native.WtTextDesc * len(lengths))()
+    for i, (n, s) in enumerate(zip(lengths, sigmas)):
+        arr[i].n = int(n)
+        arr[i].sigma = int(s)
+    out = ctypes.c_size_t(0)
+    _check(lib().wt_batched_workspace_size(kind, symtype, arr, len(lengths), ctypes.byref(out)),
+           "wt_batched_workspace_size")
+    return out.value
+
+
+def wt_build_batched(kind: int, texts, sigmas, bvs=None, zeros=None, ws=None, stream=None):
+    """Build many texts in one call.  Returns (bvs, zeros or None)."""
+    torch = _torch()
+    if not texts:
+        return [], ([] if kind == WT_MATRIX else None)
+    st = _symtype(texts[0])
+    dev = texts[0].device
+    if bvs is None:
+        bvs = [torch.empty((wt_levels(s), wt_words_per_level(t.numel())), dtype=torch.int64,
+                           device=dev) for t, s in zip(texts, sigmas)]
+    if kind == WT_MATRIX and zeros is None:
+        zeros = [torch.empty((max(wt_levels(s), 1),), dtype=torch.int64, device=dev) for s in sigmas]
+    if ws is None:
+        sz = wt_batched_workspace_size(kind, st, [t.numel() for t in texts], sigmas)
+        ws = torch.empty((max(sz, 1),), dtype=torch.uint8, device=dev)
+    arr = _descs(texts, sigmas, bvs, zeros if kind == WT_MATRIX else None)
+    _check(lib().wt_build_batched(kind, st, arr, len(texts), _ptr(ws), ws.numel(), _stream(stream)),
+           "wt_build_batched")
+    return bvs, (zeros if kind == WT_MATRIX else None)

@@ -1,0 +1,97 @@
+// Internal definitions shared by the CUDA translation units of wt_gb300.
+//
+// Construction is organised in rounds of at most 8 levels (levels 8r .. 8r+7).
+// Round r works on "jobs": contiguous runs of symbols of one text whose
+// remaining rb = L - 8r code bits are still to be split.  Round 0 has one job
+// per text.  For the wavelet matrix every round has one job per text (the text
+// stably re-sorted by the reversed 8r-bit prefix, Obs. 2).  For the wavelet
+// tree, round r >= 1 has one job per (8r)-bit prefix: the independent subtree
+// below that prefix (Sec. 2, node definition), stored contiguously because the
+// previous round wrote the text stably sorted by prefix (Obs. 1).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/wt_gb300.h"
+
+namespace wtg {
+
+constexpr int kMaxRounds = 4;         // L <= 32
+constexpr int kChunk = 8;             // levels per round
+constexpr int kThreads = 512;         // build / histogram block size
+constexpr int kWarps = kThreads / 32;
+constexpr int kTilesPerGroup = 4;     // tiles one build block processes
+constexpr int kRowsPerBlock = 64;     // groups per block of the segmented scan
+constexpr int kCols = 256;            // histogram columns (2^8 classes per round)
+constexpr int kMaxTreeSigmaLog = 24;  // WT alphabets up to 2^24
+
+// Elements per thread and tile size, by the width of an element in shared memory.
+__host__ __device__ constexpr int elems_per_thread(int width) { return width == 1 ? 32 : 16; }
+__host__ __device__ constexpr int tile_elems(int width) { return kThreads * elems_per_thread(width); }
+__host__ __device__ constexpr int group_elems(int width) { return tile_elems(width) * kTilesPerGroup; }
+
+// Smallest storage width (bytes) that holds b-bit codes.
+__host__ __device__ inline uint32_t width_for_bits(uint32_t b) { return b <= 8 ? 1u : (b <= 16 ? 2u : 4u); }
+
+struct TextInfo {
+    const void *text;        // caller's symbols (round 0 input)
+    void *buf[2];            // re-sorted symbols: round r writes buf[r & 1]
+    uint64_t *bv;            // L * W words
+    uint64_t *zeros;         // WM: L values
+    uint64_t n;
+    uint64_t W;
+    uint64_t sigma;
+    uint32_t L;
+    uint32_t in_w;
+    uint32_t slot_base[kMaxRounds];   // first job slot of this text in round r
+    uint32_t nslots[kMaxRounds];      // job slots of this text in round r (0: not taking part)
+};
+
+struct Job {
+    uint32_t n;              // symbols of this job
+    uint32_t off;            // first symbol inside the text's round buffer == first bit inside its levels
+    uint32_t text;
+    uint32_t g0;             // first group (build block) of this job in the round
+    uint32_t ng;             // groups of this job
+    uint32_t pad;
+};
+
+struct Ctl {
+    uint32_t status;                      // first device-detected error (wt_status)
+    uint32_t total_groups[kMaxRounds];
+    uint32_t pad[11];
+};
+
+struct RoundArgs {
+    Ctl *ctl;
+    const TextInfo *texts;
+    Job *jobs;               // this round's slots
+    const Job *pjobs;        // previous round's slots (WT children)
+    uint32_t *jobhist;       // [slots][256]: class totals of each job
+    const uint32_t *pjobhist;
+    uint32_t *ghist;         // [groups][256]: class counts of each group
+    uint32_t *gexcl;         // [groups][256]: count of the class in earlier groups of the job
+    uint32_t *btail;         // [blocks][256]: segmented-scan block summaries
+    uint32_t *bflag;         // [blocks]
+    uint32_t *bcarry;        // [blocks][256]
+    uint32_t ntexts;
+    uint32_t nslots;         // slots in this round
+    uint32_t pnslots;        // slots in the previous round
+    uint32_t round;
+    uint32_t kind;           // WT_TREE / WT_MATRIX
+    uint32_t gelems;         // symbols per group in this round
+    uint32_t groups_ub;      // grid bound for per-group kernels
+    uint32_t blocks_ub;      // grid bound for per-block kernels
+};
+
+// Launches one round on the stream.  Returns a CUDA error code.
+cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s);
+
+// Device pass that marks every text's Z as zero (WM) before round 0.
+cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s);
+
+cudaError_t configure_kernels();
+
+}  // namespace wtg

@@ -1,0 +1,669 @@
+// Kernels of the bottom-up prefix-counting construction (arXiv:1702.07578).
+//
+// Per round (at most 8 levels, see wt_internal.h) the work is:
+//   k_root_jobs / k_child_jobs   job list of the round
+//   k_scan_groups                groups (build blocks) per job -> first group index
+//   k_hist        (a1)           class histogram of every group; symbol range check
+//   k_blocksum, k_blockscan, k_groupexcl  (a3)
+//                                zero-based prefix sum over groups of the same job in
+//                                (class-major, group-minor) order (Alg. 2, Sec. 3.2.1);
+//                                job totals
+//   k_build       (a2-a5)        per tile: fold the histograms to every level and take
+//                                the interval starts (id or bit-reversal order,
+//                                Sec. 3.1 / 5.1); stable one-bit splits of the tile in
+//                                shared memory give, level by level, the bits of each
+//                                interval in text order; ballots pack them into words
+//                                that are copied to their interval starts; the last
+//                                split writes the symbols re-sorted for the next round.
+#include <cstdio>
+
+#include "wt_internal.h"
+
+namespace wtg {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t load_sym(const void *base, uint32_t w, uint64_t i)
+{
+    if (w == 1) return static_cast<const uint8_t *>(base)[i];
+    if (w == 2) return static_cast<const uint16_t *>(base)[i];
+    return static_cast<const uint32_t *>(base)[i];
+}
+
+__device__ __forceinline__ void store_sym(void *base, uint32_t w, uint64_t i, uint32_t v)
+{
+    if (w == 1) static_cast<uint8_t *>(base)[i] = static_cast<uint8_t>(v);
+    else if (w == 2) static_cast<uint16_t *>(base)[i] = static_cast<uint16_t>(v);
+    else static_cast<uint32_t *>(base)[i] = v;
+}
+
+// pi_l(q): the l-bit reversal of q (Sec. 5).
+__device__ __forceinline__ uint32_t rev_bits(uint32_t q, uint32_t l)
+{
+    return l ? (__brev(q) >> (32u - l)) : 0u;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+struct RoundText {
+    const void *in;   // first symbol of the text in this round's input
+    uint32_t in_w;
+    void *cut;        // re-sorted output of this round (nullptr in the last round)
+    uint32_t cut_w;
+    uint32_t rb;      // code bits still to split
+    uint32_t h;       // levels in this round
+    uint32_t c;       // first level of this round
+};
+
+__device__ __forceinline__ RoundText round_text(const TextInfo &t, uint32_t r)
+{
+    RoundText x;
+    x.c = kChunk * r;
+    x.rb = t.L - x.c;
+    x.h = x.rb < (uint32_t)kChunk ? x.rb : (uint32_t)kChunk;
+    x.in = r == 0 ? t.text : t.buf[(r - 1) & 1];
+    x.in_w = r == 0 ? t.in_w : width_for_bits(x.rb);
+    x.cut = x.rb > x.h ? t.buf[r & 1] : nullptr;
+    x.cut_w = width_for_bits(x.rb - x.h);
+    return x;
+}
+
+// The slot owning group g: the last slot whose first group is <= g (slots are
+// in increasing g0 order; empty slots share g0 with their successor).
+__device__ __forceinline__ uint32_t find_slot(const Job *jobs, uint32_t nslots, uint32_t g)
+{
+    uint32_t lo = 0, hi = nslots;           // first slot with g0 > g
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (jobs[mid].g0 <= g) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
+}
+
+// Calls f(local_index, symbol) for the symbols [i0, i1) of base, spread over the
+// block; full 16-byte chunks are read with vector loads.
+template <typename F>
+__device__ __forceinline__ void for_range(const void *base, uint32_t w, uint64_t i0, uint64_t i1, F f)
+{
+    const uint8_t *b = static_cast<const uint8_t *>(base);
+    uintptr_t lo = reinterpret_cast<uintptr_t>(b) + i0 * w;
+    uintptr_t hi = reinterpret_cast<uintptr_t>(b) + i1 * w;
+    uintptr_t alo = (lo + 15) & ~uintptr_t(15), ahi = hi & ~uintptr_t(15);
+    if (alo >= ahi) {
+        for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) f(uint32_t(i - i0), load_sym(base, w, i));
+        return;
+    }
+    uint64_t head = (alo - lo) / w;          // symbols before the first full chunk
+    uint64_t tail0 = (ahi - reinterpret_cast<uintptr_t>(b)) / w;   // first symbol after the last chunk
+    for (uint64_t i = i0 + threadIdx.x; i < i0 + head; i += blockDim.x) f(uint32_t(i - i0), load_sym(base, w, i));
+    for (uint64_t i = tail0 + threadIdx.x; i < i1; i += blockDim.x) f(uint32_t(i - i0), load_sym(base, w, i));
+    const uint4 *v = reinterpret_cast<const uint4 *>(alo);
+    uint64_t nchunks = (ahi - alo) >> 4;
+    uint32_t per = 16u / w;
+    for (uint64_t k = threadIdx.x; k < nchunks; k += blockDim.x) {
+        uint4 q = __ldg(v + k);
+        uint32_t words[4] = {q.x, q.y, q.z, q.w};
+        uint32_t li = uint32_t(head + k * per);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t x = words[j];
+            if (w == 1) {
+                f(li + 4 * j + 0, x & 0xffu);
+                f(li + 4 * j + 1, (x >> 8) & 0xffu);
+                f(li + 4 * j + 2, (x >> 16) & 0xffu);
+                f(li + 4 * j + 3, x >> 24);
+            } else if (w == 2) {
+                f(li + 2 * j + 0, x & 0xffffu);
+                f(li + 2 * j + 1, x >> 16);
+            } else {
+                f(li + j, x);
+            }
+        }
+    }
+}
+
+// Exclusive scan of n <= 256 values by one warp: out[map(i)] = sum of
+// val(map(j)) for j < i.  Each lane takes 8 consecutive positions.
+template <typename V, typename M, typename O>
+__device__ __forceinline__ uint32_t warp_scan_256(uint32_t n, V val, M map, O out)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t loc[8];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        uint32_t i = lane * 8 + k;
+        loc[k] = i < n ? val(map(i)) : 0u;
+        sum += loc[k];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, inc, d);
+        if (lane >= (uint32_t)d) inc += y;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        uint32_t i = lane * 8 + k;
+        if (i < n) out(map(i), run);
+        run += loc[k];
+    }
+    return __shfl_sync(kFull, inc, 31);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// job lists
+
+__global__ void k_zero_z(const TextInfo *texts, uint32_t ntexts)
+{
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntexts) return;
+    const TextInfo &x = texts[t];
+    if (x.zeros)
+        for (uint32_t l = 0; l < x.L; ++l) x.zeros[l] = 0;
+}
+
+// One job per taking-part text (round 0, and every WM round).
+__global__ void k_root_jobs(RoundArgs a)
+{
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.ntexts) return;
+    const TextInfo &x = a.texts[t];
+    if (x.nslots[a.round] == 0) return;
+    Job j;
+    j.n = (uint32_t)x.n;
+    j.off = 0;
+    j.text = t;
+    j.g0 = 0;
+    j.ng = (uint32_t)((x.n + a.gelems - 1) / a.gelems);
+    j.pad = 0;
+    a.jobs[x.slot_base[a.round]] = j;
+}
+
+// WT round r >= 1: parent job p splits into 256 children, one per class of the
+// parent's last level; child q starts at the parent's start plus the
+// zero-based prefix sum of the parent's class totals in id order (Sec. 3.1).
+__global__ void __launch_bounds__(256) k_child_jobs(RoundArgs a)
+{
+    __shared__ uint32_t s[256];
+    uint32_t p = blockIdx.x;
+    const Job pj = a.pjobs[p];
+    const TextInfo &x = a.texts[pj.text];
+    if (x.nslots[a.round] == 0) return;
+    uint32_t q = threadIdx.x;
+    uint32_t cnt = pj.ng ? a.pjobhist[(size_t)p * kCols + q] : 0u;
+    s[q] = cnt;
+    __syncthreads();
+    if (q < 32) {
+        warp_scan_256(256, [&](uint32_t i) { return s[i]; }, [](uint32_t i) { return i; },
+                      [&](uint32_t i, uint32_t v) { s[i] = v; });
+    }
+    __syncthreads();
+    uint32_t cb = x.slot_base[a.round] + (p - x.slot_base[a.round - 1]) * 256u;
+    Job j;
+    j.n = cnt;
+    j.off = pj.off + s[q];
+    j.text = pj.text;
+    j.g0 = 0;
+    j.ng = (cnt + a.gelems - 1) / a.gelems;
+    j.pad = 0;
+    a.jobs[cb + q] = j;
+}
+
+// Exclusive scan of the group counts over all slots -> g0; total groups.
+__global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
+{
+    __shared__ uint32_t part[1024];
+    uint32_t n = a.nslots;
+    uint32_t per = (n + 1023) / 1024;
+    uint32_t b = threadIdx.x * per, e = min(n, b + per);
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += a.jobs[i].ng;
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (uint32_t d = 1; d < 1024; d <<= 1) {
+        uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum;
+    for (uint32_t i = b; i < e; ++i) {
+        a.jobs[i].g0 = run;
+        run += a.jobs[i].ng;
+    }
+    if (threadIdx.x == 1023) a.ctl->total_groups[a.round] = part[1023];
+}
+
+// ---------------------------------------------------------------------------
+// a1: class histogram of every group (the first counting-sort phase)
+
+__global__ void __launch_bounds__(kThreads) k_hist(RoundArgs a)
+{
+    __shared__ uint32_t wh[kWarps][kCols];
+    const uint32_t g = blockIdx.x;
+    if (g >= a.ctl->total_groups[a.round]) return;
+    const uint32_t slot = find_slot(a.jobs, a.nslots, g);
+    const Job jb = a.jobs[slot];
+    const TextInfo &t = a.texts[jb.text];
+    const RoundText rt = round_text(t, a.round);
+    for (uint32_t i = threadIdx.x; i < kWarps * kCols; i += kThreads) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t i0 = (uint64_t)(g - jb.g0) * a.gelems;
+    const uint64_t i1 = min((uint64_t)jb.n, i0 + a.gelems);
+    const uint32_t shift = rt.rb - rt.h, mask = (1u << rt.h) - 1u;
+    const bool check = a.round == 0 && t.sigma < (1ull << t.L);
+    const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
+    uint32_t *mine = wh[threadIdx.x >> 5];
+    bool bad = false;
+    const uint8_t *base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
+    for_range(base, rt.in_w, i0, i1, [&](uint32_t, uint32_t v) {
+        bad |= check && v >= sig;
+        bad |= a.round == 0 && t.L < 32 && (v >> t.L) != 0;
+        atomicAdd(&mine[(v >> shift) & mask], 1u);
+    });
+    if (bad) atomicCAS(&a.ctl->status, 0u, (uint32_t)WT_ERR_SYMBOL_RANGE);
+    __syncthreads();
+    for (uint32_t col = threadIdx.x; col < kCols; col += kThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += wh[w][col];
+        a.ghist[(size_t)g * kCols + col] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3: segmented exclusive scan of the group histograms (segments = jobs)
+
+__global__ void __launch_bounds__(256) k_blocksum(RoundArgs a)
+{
+    __shared__ uint8_t first[kRowsPerBlock];
+    const uint32_t total = a.ctl->total_groups[a.round];
+    const uint32_t b = blockIdx.x, r0 = b * kRowsPerBlock;
+    if (r0 >= total) return;
+    const uint32_t rows = min((uint32_t)kRowsPerBlock, total - r0);
+    if (threadIdx.x < rows) {
+        uint32_t g = r0 + threadIdx.x;
+        first[threadIdx.x] = a.jobs[find_slot(a.jobs, a.nslots, g)].g0 == g;
+    }
+    __syncthreads();
+    const uint32_t col = threadIdx.x;
+    uint32_t tail = 0, has = 0;
+    for (uint32_t r = 0; r < rows; ++r) {
+        if (first[r]) { tail = 0; has = 1; }
+        tail += a.ghist[(size_t)(r0 + r) * kCols + col];
+    }
+    a.btail[(size_t)b * kCols + col] = tail;
+    if (col == 0) a.bflag[b] = has;
+}
+
+__global__ void __launch_bounds__(256) k_blockscan(RoundArgs a)
+{
+    const uint32_t total = a.ctl->total_groups[a.round];
+    const uint32_t nb = (total + kRowsPerBlock - 1) / kRowsPerBlock;
+    const uint32_t col = threadIdx.x;
+    uint32_t carry = 0;
+    uint32_t b = 0;
+    for (; b + 8 <= nb; b += 8) {
+        uint32_t t[8], f[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            t[k] = a.btail[(size_t)(b + k) * kCols + col];
+            f[k] = a.bflag[b + k];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            a.bcarry[(size_t)(b + k) * kCols + col] = carry;
+            carry = f[k] ? t[k] : carry + t[k];
+        }
+    }
+    for (; b < nb; ++b) {
+        a.bcarry[(size_t)b * kCols + col] = carry;
+        uint32_t t = a.btail[(size_t)b * kCols + col];
+        carry = a.bflag[b] ? t : carry + t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_groupexcl(RoundArgs a)
+{
+    __shared__ uint32_t slot_of[kRowsPerBlock];
+    __shared__ uint8_t first[kRowsPerBlock], last[kRowsPerBlock];
+    const uint32_t total = a.ctl->total_groups[a.round];
+    const uint32_t b = blockIdx.x, r0 = b * kRowsPerBlock;
+    if (r0 >= total) return;
+    const uint32_t rows = min((uint32_t)kRowsPerBlock, total - r0);
+    if (threadIdx.x < rows) {
+        uint32_t g = r0 + threadIdx.x;
+        uint32_t s = find_slot(a.jobs, a.nslots, g);
+        const Job j = a.jobs[s];
+        slot_of[threadIdx.x] = s;
+        first[threadIdx.x] = j.g0 == g;
+        last[threadIdx.x] = j.g0 + j.ng - 1 == g;
+    }
+    __syncthreads();
+    const uint32_t col = threadIdx.x;
+    uint32_t run = a.bcarry[(size_t)b * kCols + col];
+    for (uint32_t r = 0; r < rows; ++r) {
+        if (first[r]) run = 0;
+        a.gexcl[(size_t)(r0 + r) * kCols + col] = run;
+        run += a.ghist[(size_t)(r0 + r) * kCols + col];
+        if (last[r]) a.jobhist[(size_t)slot_of[r] * kCols + col] = run;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a2, a4, a5: interval starts, stable splits, packed bit writes, re-sorted symbols
+
+namespace {
+
+// Heap layout of per-level class tables: entry (1 << l) + q for class q of level l.
+constexpr int kHeap = 512;
+
+template <typename E>
+struct BuildSmem {
+    static constexpr int R = elems_per_thread(sizeof(E));
+    static constexpr int S = tile_elems(sizeof(E));
+    E buf[2][S];
+    uint32_t lvl[S / 32 + 4];          // packed bits of the current level, tile order
+    uint32_t whist[kWarps][kCols];     // per-warp class counts of the tile
+    uint32_t thist[kCols];             // class counts of the tile
+    uint32_t offq[kCols];              // class counts of the job before this tile
+    uint32_t jP[kCols + 1];            // prefix sums (job totals, tile counts, offsets)
+    uint32_t tP[kCols + 1];
+    uint32_t oP[kCols + 1];
+    uint32_t jcnt[kHeap];              // job class totals per level
+    uint32_t jspos[kHeap];             // interval starts inside the job per level
+    uint32_t tcnt[kHeap];              // tile class counts per level
+    uint32_t loc[kHeap];               // class start inside the tile (tile order)
+    uint32_t glo[kHeap];               // class start inside the text's level (bits)
+    uint32_t wpre[kHeap];              // prefix of destination words per level
+    uint32_t wtot[kChunk + 2];
+    uint32_t wones[kWarps];
+};
+
+// Up to 64 bits of the tile's packed level starting at bit p.
+__device__ __forceinline__ uint64_t extract_bits(const uint32_t *lvl, uint32_t p, uint32_t k)
+{
+    uint32_t w0 = p >> 5, s = p & 31u;
+    uint64_t lo = ((uint64_t)lvl[w0 + 1] << 32) | lvl[w0];
+    uint64_t r = lo >> s;
+    if (s) r |= (uint64_t)lvl[w0 + 2] << (64u - s);
+    if (k < 64) r &= (1ull << k) - 1ull;
+    return r;
+}
+
+}  // namespace
+
+template <typename E>
+__global__ void __launch_bounds__(kThreads, 2) k_build(RoundArgs a)
+{
+    using SM = BuildSmem<E>;
+    constexpr int R = SM::R;
+    constexpr int S = SM::S;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    SM &sm = *reinterpret_cast<SM *>(smem_raw);
+
+    const uint32_t g = blockIdx.x;
+    if (g >= a.ctl->total_groups[a.round]) return;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t slot = find_slot(a.jobs, a.nslots, g);
+    const Job jb = a.jobs[slot];
+    const TextInfo &t = a.texts[jb.text];
+    const RoundText rt = round_text(t, a.round);
+    const uint32_t h = rt.h, rb = rt.rb;
+    const uint32_t gi = g - jb.g0;
+    const bool matrix = a.kind == WT_MATRIX;
+    const bool has_cut = rt.cut != nullptr;
+
+    // job totals -> per-level class totals and interval starts (fold, Alg. 1;
+    // zero-based prefix sum in id or pi_l order, Sec. 3.1 / 5.1)
+    for (uint32_t q = tid; q < kCols; q += kThreads) {
+        sm.thist[q] = a.jobhist[(size_t)slot * kCols + q];
+        sm.offq[q] = a.gexcl[(size_t)g * kCols + q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.thist[i]; },
+                                     [](uint32_t i) { return i; },
+                                     [&](uint32_t i, uint32_t v) { sm.jP[i] = v; });
+        if (lane == 0) sm.jP[256] = tot;
+    }
+    __syncthreads();
+    for (uint32_t idx = tid; idx < kHeap; idx += kThreads) {
+        if (idx == 0) continue;
+        uint32_t l = 31u - __clz(idx), q = idx - (1u << l);
+        if (l <= h) {
+            uint32_t s = h - l;
+            sm.jcnt[idx] = sm.jP[(q + 1) << s] - sm.jP[q << s];
+        }
+    }
+    __syncthreads();
+    if (warp <= h) {
+        const uint32_t l = warp, base = 1u << l;
+        warp_scan_256(base, [&](uint32_t q) { return sm.jcnt[base + q]; },
+                      [&](uint32_t i) { return matrix ? rev_bits(i, l) : i; },
+                      [&](uint32_t q, uint32_t v) { sm.jspos[base + q] = v; });
+    }
+    if (matrix && gi == 0 && tid < h) {        // Z[c + l]: even (l+1)-prefixes
+        const uint32_t l = tid, base = 2u << l;
+        uint32_t z = 0;
+        for (uint32_t p = 0; p < base; p += 2) z += sm.jcnt[base + p];
+        t.zeros[rt.c + l] = z;
+    }
+    __syncthreads();
+
+    const uint64_t g_begin = (uint64_t)gi * a.gelems;
+    const uint64_t g_end = min((uint64_t)jb.n, g_begin + a.gelems);
+    const uint8_t *in_base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
+    const uint32_t shift = rb - h, cmask = (1u << h) - 1u;
+
+    for (uint64_t t0 = g_begin; t0 < g_end; t0 += S) {
+        const uint32_t m = (uint32_t)min((uint64_t)S, g_end - t0);
+        // ---- load the tile (text order) and count its classes
+        for (uint32_t i = tid; i < kWarps * kCols; i += kThreads) (&sm.whist[0][0])[i] = 0;
+        __syncthreads();
+        {
+            uint32_t *mine = sm.whist[warp];
+            E *dst = sm.buf[0];
+            for_range(in_base, rt.in_w, t0, t0 + m, [&](uint32_t li, uint32_t v) {
+                dst[li] = static_cast<E>(v);
+                atomicAdd(&mine[(v >> shift) & cmask], 1u);
+            });
+        }
+        __syncthreads();
+        for (uint32_t q = tid; q < kCols; q += kThreads) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) s += sm.whist[w][q];
+            sm.thist[q] = s;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.thist[i]; },
+                                         [](uint32_t i) { return i; },
+                                         [&](uint32_t i, uint32_t v) { sm.tP[i] = v; });
+            if (lane == 0) sm.tP[256] = tot;
+        } else if (warp == 1) {
+            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.offq[i]; },
+                                         [](uint32_t i) { return i; },
+                                         [&](uint32_t i, uint32_t v) { sm.oP[i] = v; });
+            if (lane == 0) sm.oP[256] = tot;
+        }
+        __syncthreads();
+        for (uint32_t idx = tid; idx < kHeap; idx += kThreads) {
+            if (idx == 0) continue;
+            uint32_t l = 31u - __clz(idx), q = idx - (1u << l);
+            if (l <= h) {
+                uint32_t s = h - l, lo = q << s, hi = (q + 1) << s;
+                sm.tcnt[idx] = sm.tP[hi] - sm.tP[lo];
+                sm.glo[idx] = jb.off + sm.jspos[idx] + (sm.oP[hi] - sm.oP[lo]);
+            }
+        }
+        __syncthreads();
+        if (warp <= h) {
+            const uint32_t l = warp, base = 1u << l;
+            // tile order after l splits: classes by reversed prefix
+            warp_scan_256(base, [&](uint32_t q) { return sm.tcnt[base + q]; },
+                          [&](uint32_t i) { return rev_bits(i, l); },
+                          [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
+            uint32_t wt = warp_scan_256(
+                base,
+                [&](uint32_t q) {
+                    uint32_t c = sm.tcnt[base + q];
+                    if (c == 0) return 0u;
+                    uint32_t s = sm.glo[base + q];
+                    return ((s + c - 1) >> 6) - (s >> 6) + 1u;
+                },
+                [](uint32_t i) { return i; },
+                [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
+            if (lane == 0) sm.wtot[l] = wt;
+        } else if (warp == kWarps - 1) {
+            for (uint32_t q = lane; q < kCols; q += 32) sm.offq[q] += sm.thist[q];
+        }
+        __syncthreads();
+
+        // ---- levels of this round
+        for (uint32_t l = 0; l < h; ++l) {
+            const E *cur = sm.buf[l & 1];
+            E *nxt = sm.buf[(l + 1) & 1];
+            const uint32_t sh = rb - 1u - l;
+            uint32_t e[R];
+            uint32_t ones = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                uint32_t idx = (warp * R + r) * 32u + lane;
+                uint32_t v = idx < m ? (uint32_t)cur[idx] : 0u;
+                e[r] = v;
+                uint32_t B = __ballot_sync(kFull, (v >> sh) & 1u);
+                if (lane == 0) sm.lvl[warp * R + r] = B;
+                ones += __popc(B);
+            }
+            if (lane == 0) sm.wones[warp] = ones;
+            __syncthreads();
+
+            // copy every class's bits to its interval start in level c + l
+            {
+                const uint32_t base = 1u << l, wt = sm.wtot[l];
+                uint64_t *lv = t.bv + (uint64_t)(rt.c + l) * t.W;
+                for (uint32_t k = tid; k < wt; k += kThreads) {
+                    uint32_t lo = 0, hi = base;     // last class with wpre <= k
+                    while (hi - lo > 1) {
+                        uint32_t mid = (lo + hi) >> 1;
+                        if (sm.wpre[base + mid] <= k) lo = mid; else hi = mid;
+                    }
+                    const uint32_t idx = base + lo;
+                    const uint64_t gs = sm.glo[idx], ge = gs + sm.tcnt[idx];
+                    const uint64_t word = (gs >> 6) + (k - sm.wpre[idx]);
+                    const uint64_t wb = word << 6;
+                    const uint32_t blo = (uint32_t)((gs > wb ? gs : wb) - wb);
+                    uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
+                    const uint32_t src = sm.loc[idx] + (uint32_t)(wb + blo - gs);
+                    const uint64_t val = extract_bits(sm.lvl, src, bhi - blo) << blo;
+                    if (ge == t.n) bhi = 64;       // bits past n belong to the last interval
+                    if (blo == 0 && bhi == 64) {
+                        lv[word] = val;
+                    } else {
+                        const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
+                        atomicAnd(reinterpret_cast<unsigned long long *>(lv + word), ~msk);
+                        atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
+                    }
+                }
+            }
+
+            if (l + 1 < h || has_cut) {
+                // stable split by bit l: zeros keep their order first, then ones
+                uint32_t x = lane < (uint32_t)kWarps ? sm.wones[lane] : 0u;
+                uint32_t inc = x;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    uint32_t y = __shfl_up_sync(kFull, inc, d);
+                    if (lane >= (uint32_t)d) inc += y;
+                }
+                const uint32_t total = __shfl_sync(kFull, inc, kWarps - 1);
+                uint32_t run = warp ? __shfl_sync(kFull, inc, warp - 1) : 0u;
+                const uint32_t zt = m - total;
+                const uint32_t lt = lanemask_lt();
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t idx = (warp * R + r) * 32u + lane;
+                    const uint32_t B = sm.lvl[warp * R + r];
+                    const uint32_t rk = run + __popc(B & lt);
+                    const uint32_t pos = ((e[r] >> sh) & 1u) ? zt + rk : idx - rk;
+                    if (idx < m) nxt[pos] = static_cast<E>(e[r]);
+                    run += __popc(B);
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- re-sorted symbols for the next round (stable counting sort by the
+        //      round's 8-bit class, Alg. 2; WM: reversed order, Obs. 2)
+        if (has_cut) {
+            const E *fin = sm.buf[h & 1];
+            const uint32_t base = 1u << h;
+            const uint32_t low = (1u << (rb - h)) - 1u;
+            for (uint32_t i = tid; i < m; i += kThreads) {
+                const uint32_t v = fin[i];
+                const uint32_t idx = base + ((v >> shift) & cmask);
+                const uint64_t dst = (uint64_t)sm.glo[idx] + (i - sm.loc[idx]);
+                store_sym(rt.cut, rt.cut_w, dst, v & low);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+cudaError_t configure_kernels()
+{
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_build<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BuildSmem<uint8_t>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_build<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BuildSmem<uint16_t>));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_build<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(BuildSmem<uint32_t>));
+}
+
+cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s)
+{
+    if (ntexts == 0) return cudaSuccess;
+    k_zero_z<<<(ntexts + 255) / 256, 256, 0, s>>>(texts, ntexts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s)
+{
+    if (a.nslots == 0) return cudaSuccess;
+    const bool root = a.round == 0 || a.kind == WT_MATRIX;
+    if (root) k_root_jobs<<<(a.ntexts + 255) / 256, 256, 0, s>>>(a);
+    else k_child_jobs<<<a.pnslots, 256, 0, s>>>(a);
+    k_scan_groups<<<1, 1024, 0, s>>>(a);
+    if (a.groups_ub == 0) return cudaGetLastError();
+    k_hist<<<a.groups_ub, kThreads, 0, s>>>(a);
+    k_blocksum<<<a.blocks_ub, 256, 0, s>>>(a);
+    k_blockscan<<<1, 256, 0, s>>>(a);
+    k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
+    if (smem_width == 1)
+        k_build<uint8_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint8_t>), s>>>(a);
+    else if (smem_width == 2)
+        k_build<uint16_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint16_t>), s>>>(a);
+    else
+        k_build<uint32_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint32_t>), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace wtg

@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/wt_gb300.h declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import paper_1702_07578_gb300 as wtg
+from paper_1702_07578_gb300 import _native
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "wt_gb300.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*\b((?:wt|wm)_[a-z_]+)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("wt_build", "wm_build", "wt_build_batched", "wt_workspace_size",
+                 "wt_server_create", "wt_server_submit", "wt_sync_status"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = _native.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(\w+)", out))
+    assert set(declared_functions()) <= exported
+    assert set(_native.SIGNATURES) == set(declared_functions())
+
+
+def test_host_only_calls():
+    assert wtg.wt_levels(1) == 0 and wtg.wt_levels(2) == 1 and wtg.wt_levels(256) == 8
+    assert wtg.wt_levels(257) == 9 and wtg.wt_levels(1 << 20) == 20
+    assert wtg.wt_words_per_level(0) == 0 and wtg.wt_words_per_level(65) == 2
+    assert wtg.wt_status_string(2) == "symbol out of range"
+    assert wtg.wt_workspace_size(wtg.WT_TREE, wtg.WT_U8, 1 << 20, 256) > 0
+    import pytest
+    with pytest.raises(wtg.WtError):
+        wtg.wt_workspace_size(wtg.WT_TREE, wtg.WT_U8, 10, 0)
+    with pytest.raises(wtg.WtError):
+        wtg.wt_workspace_size(wtg.WT_TREE, wtg.WT_U8, 10, 300)
+    with pytest.raises(wtg.WtError):
+        wtg.wt_workspace_size(wtg.WT_TREE, wtg.WT_U32, 10, 1 << 25)
+    assert wtg.wt_workspace_size(wtg.WT_MATRIX, wtg.WT_U32, 10, 1 << 32) > 0
+    sz = wtg.wt_batched_workspace_size(wtg.WT_TREE, wtg.WT_U16, [1000, 5000], [16, 65536])
+    assert sz > 0
+
+
+def test_compiled_for_sm103a_only():
+    """The build uses exactly one -gencode, for sm_103a."""
+    assert _native.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
