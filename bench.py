@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: bottom-up wavelet tree + wavelet matrix construction on GB300.
+
+One step = one wavelet tree build and one wavelet matrix build (wt_build then
+wm_build through the C ABI) of the same resident text.  The default workload is
+n = 2^30 uint8 symbols over sigma = 256, Zipf(1.0) over a seeded permutation
+(byte-text-like skew; synthetic stand-in for the paper's byte texts).
+
+Prints one JSON line.  ``value`` is input symbols built per second over all
+ranks (2 * n per step per rank: each of the two builds consumes the n-symbol
+text).  Inputs (1 GiB) are larger than L2, so no flush is needed between steps.
+
+--impl reference   times the CPU oracle (the plain top-down construction from
+                   the definitions) on a bounded sample of the same workload.
+--workload         bytes (default) | small | large_alphabet | batched
+Multi-GPU: one process per GPU (torchrun); every rank builds its own replica
+of the workload (independent texts, no collective in the data path); rank 0
+prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input symbols/s, WT+WM construction (n=2^30 u8, sigma=256)"
+UNIT = "symbols/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (barrier / max over ranks only; no data-path collective)
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as tdist
+        backend = "nccl" if _cuda() else "gloo"
+        tdist.init_process_group(backend=backend)
+        pg = tdist
+    return rank, local, ws, pg
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for name, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+
+def load_workload(name, n_log2=None):
+    import synth
+    if name == "bytes":
+        k = 30 if n_log2 is None else n_log2
+        T, sigma = synth.workload_bytes(1 << k)
+        desc = f"WT+WM, n=2^{k} uint8, sigma=256, Zipf(1.0) over a seeded permutation"
+    elif name == "small":
+        T, sigma = synth.workload_small()
+        desc = "WT+WM, n=2^20 uint8, sigma=256, i.i.d. uniform"
+    elif name == "large_alphabet":
+        k = 28 if n_log2 is None else n_log2
+        T, sigma = synth.workload_large_alphabet(1 << k)
+        desc = f"WT+WM, n=2^{k} uint32, sigma=2^20, half uniform / half order-1 Markov"
+    else:
+        raise ValueError(name)
+    return T, sigma, desc
+
+
+def cpu_baseline(T, sigma, sample_log2):
+    """The oracle as it stands (single thread) on the first 2^k symbols, WT then WM."""
+    import oracle
+    oracle.build()
+    S = T[: min(T.size, 1 << sample_log2)]
+    t0 = time.perf_counter()
+    oracle.wt(S, sigma)
+    oracle.wm(S, sigma)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * S.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 2^{int(np.log2(S.size))} symbols of the workload, WT + WM "
+                      f"(oracle top-down construction, 1 thread; {dt:.1f} s; host has "
+                      f"{os.cpu_count()} cores)"}
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, _, ws, pg = dist()
+    if rank != 0:
+        return 0
+    T, sigma, desc = load_workload(args.workload, args.n_log2)
+    import oracle
+    oracle.build()
+    k = args.oracle_sample_log2
+    S = T[: min(T.size, 1 << k)]
+    for _ in range(args.warmup):
+        oracle.wt(S[: min(S.size, 1 << 16)], sigma)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.wt(S, sigma)
+        oracle.wm(S, sigma)
+        times.append(time.perf_counter() - t0)
+    per = statistics.median(times)
+    v = 2 * S.size / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": desc, "sample": f"first 2^{k} symbols"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first 2^{k} symbols per step, WT + WM, 1 thread"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1702_07578_gb300 as wtg
+
+    rank, local, world, pg = dist()
+    torch.cuda.set_device(local)
+    T, sigma, desc = load_workload(args.workload, args.n_log2)
+    n = T.size
+    w = T.dtype.itemsize
+    L = wtg.wt_levels(sigma)
+    W = wtg.wt_words_per_level(n)
+    host = torch.from_numpy(T.view({1: np.uint8, 2: np.int16, 4: np.int32}[w]))
+    text = host.cuda()
+    ws_t = torch.empty((wtg.wt_workspace_size(wtg.WT_TREE, w, n, sigma),), dtype=torch.uint8, device="cuda")
+    ws_m = torch.empty((wtg.wt_workspace_size(wtg.WT_MATRIX, w, n, sigma),), dtype=torch.uint8, device="cuda")
+    bv_t = torch.empty((L, W), dtype=torch.int64, device="cuda")
+    bv_m = torch.empty((L, W), dtype=torch.int64, device="cuda")
+    z = torch.empty((max(L, 1),), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        wtg.wt_build(text, sigma, bv=bv_t, ws=ws_t, stream=stream)
+        wtg.wm_build(text, sigma, bv=bv_m, zeros=z, ws=ws_m, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    wtg.wt_sync_status(ws_t)
+    wtg.wt_sync_status(ws_m)
+
+    clocks = ClockSampler(local)
+    wtg.wt_profile_enable(True)
+    wtg.wt_profile_read(reset=True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(pg)
+    prof = wtg.wt_profile_read(reset=True)
+    wtg.wt_profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(pg, ms)
+    value = world * 2 * n / (ms / 1e3)
+
+    # dominant kernel: the split/scatter kernel (k_build), one launch per round per build
+    peak, peak_kind = peaks()
+    b_ms, b_launch = prof["build"]
+    algo_bytes = n * w + n * L / 8.0          # one text read + L bits written per symbol
+    rounds = (L + 7) // 8
+    per_launch_bytes = algo_bytes / rounds
+    avg_build_s = (b_ms / b_launch) / 1e3 if b_launch else float("nan")
+    achieved = per_launch_bytes / avg_build_s / 1e9
+    # kernels per step: per round jobs(2) + hist(1) + scan(3) + build(1); WM adds one Z-clear kernel
+    launches = sum(v[1] for v in prof.values()) + args.steps
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": args.traffic, "kernel": "k_build",
+                "peak_kind": peak_kind}
+    step_frac = (2 * algo_bytes / (ms / 1e3) / 1e9) / peak
+    breakdown = {f: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                 for f, v in prof.items()}
+
+    # end to end through the C ABI with host buffers: H2D text, both builds, D2H results
+    pin = host.pin_memory()
+    out_t = torch.empty((L, W), dtype=torch.int64).pin_memory()
+    out_m = torch.empty((L, W), dtype=torch.int64).pin_memory()
+    out_z = torch.empty((max(L, 1),), dtype=torch.int64).pin_memory()
+    e2e_steps = max(2, args.steps // 2)
+
+    def e2e_step():
+        text.copy_(pin, non_blocking=True)
+        step()
+        out_t.copy_(bv_t, non_blocking=True)
+        out_m.copy_(bv_m, non_blocking=True)
+        out_z.copy_(z, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(pg, e0.elapsed_time(e1) / e2e_steps)
+    e2e = {"value": world * 2 * n / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * w,
+           "d2h_bytes_per_step": 2 * L * W * 8 + max(L, 1) * 8, "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8" if w == 1 else f"u{8 * w}", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "sigma": sigma, "levels": L, "builds_per_step": 2,
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world} (independent texts)"},
+        "roofline": roofline,
+        "step_roofline_frac": step_frac,
+        "breakdown": breakdown,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(T, sigma, args.oracle_sample_log2)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bytes",
+                    choices=["bytes", "small", "large_alphabet"])
+    ap.add_argument("--n-log2", type=int, default=None,
+                    help="text length 2^k (smaller cases for profiler captures)")
+    ap.add_argument("--oracle-sample-log2", type=int, default=26)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per k_build launch from an ncu capture (reported as is)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

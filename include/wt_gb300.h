@@ -32,7 +32,7 @@
  * unspecified (the kernels still write only inside the caller's buffers).
  * No call aborts the process.
  *
- * Limits: n < 2^40 per text; sigma <= 2^32 for the WM; sigma <= 2^24 for
+ * Limits: n < 2^32 per text; sigma <= 2^32 for the WM; sigma <= 2^24 for
  * the WT (larger alphabets return WT_ERR_INVALID_ARG).  The storage type
  * must hold sigma - 1 (sigma <= 2^8 for WT_U8, <= 2^16 for WT_U16).
  */
@@ -161,11 +161,31 @@ wt_status wt_server_submit(wt_server *s, const wt_request *req, uint64_t *ticket
 /* Wait until the request is built (timeout_us < 0: no limit); WT_ERR_TIMEOUT
  * if the limit passes first. */
 wt_status wt_server_wait(wt_server *s, uint64_t ticket, int64_t timeout_us, wt_result *res);
+/* Copy a finished request's bit vectors (L * W words) and, for WT_MATRIX,
+ * Z (L values) to host memory; blocks until the copy is done.  h_zeros may be
+ * NULL.  WT_ERR_BUSY if the request has not finished. */
+wt_status wt_server_read(wt_server *s, uint64_t ticket, uint64_t *h_bv, uint64_t *h_zeros);
 /* Free the request's device memory; the ticket becomes invalid. */
 wt_status wt_server_release(wt_server *s, uint64_t ticket);
 wt_status wt_server_get_stats(wt_server *s, wt_server_stats *st);
 /* Finish in-flight work, free everything. */
 void wt_server_destroy(wt_server *s);
+
+/* ---- diagnostics ----------------------------------------------------------
+ * Per-kernel device time.  While enabled, every build records CUDA events on
+ * its own stream before and after each kernel it launches (the work itself is
+ * unchanged).  wt_profile_read() waits for the recorded events and returns the
+ * summed milliseconds and launch counts per kernel family since the last
+ * reset:  [0] split/scatter (k_build)   [1] histogram (k_hist)
+ *         [2] segmented scan (3 kernels) [3] job lists (2-3 kernels).
+ * Not thread-safe with concurrent builds; meant for benchmarks. */
+typedef struct {
+    double ms[4];
+    uint64_t launches[4];
+} wt_profile;
+
+void wt_profile_enable(int on);
+wt_status wt_profile_read(wt_profile *out, int reset);
 
 #ifdef __cplusplus
 }

@@ -170,3 +170,76 @@ def wt_build_batched(kind: int, texts, sigmas, bvs=None, zeros=None, ws=None, st
     _check(lib().wt_build_batched(kind, st, arr, len(texts), _ptr(ws), ws.numel(), _stream(stream)),
            "wt_build_batched")
     return bvs, (zeros if kind == WT_MATRIX else None)
+
+
+PROFILE_FAMILIES = ("build", "hist", "scan", "jobs")
+
+
+def wt_profile_enable(on: bool = True):
+    lib().wt_profile_enable(1 if on else 0)
+
+
+def wt_profile_read(reset: bool = False):
+    """{family: (milliseconds, launches)} since the last reset (waits for the events)."""
+    p = _native.WtProfile()
+    _check(lib().wt_profile_read(ctypes.byref(p), 1 if reset else 0), "wt_profile_read")
+    return {f: (p.ms[i], int(p.launches[i])) for i, f in enumerate(PROFILE_FAMILIES)}
+
+
+class WtServer:
+    """Serving loop (wt_server_*): submit host texts, wait, read or keep results on the device."""
+
+    def __init__(self, hbm_budget_bytes: int, max_batch: int = 64, streams: int = 2,
+                 device: int = 0, max_pending: int = 0):
+        cfg = _native.WtServerConfig(int(hbm_budget_bytes), int(max_batch), int(streams),
+                                     int(device), int(max_pending))
+        h = ctypes.c_void_p()
+        _check(lib().wt_server_create(ctypes.byref(cfg), ctypes.byref(h)), "wt_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, kind: int, text, sigma: int) -> int:
+        import numpy as np
+        text = np.ascontiguousarray(text)
+        st = {1: WT_U8, 2: WT_U16, 4: WT_U32}[text.dtype.itemsize]
+        req = _native.WtRequest(kind, st, text.ctypes.data if text.size else 0, text.size, int(sigma))
+        t = ctypes.c_uint64(0)
+        _check(lib().wt_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "wt_server_submit")
+        self._keep[t.value] = (kind, text.size, int(sigma))
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        r = _native.WtResult()
+        _check(lib().wt_server_wait(self._h, ticket, int(timeout_us), ctypes.byref(r)), "wt_server_wait")
+        return {"levels": r.levels, "words_per_level": r.words_per_level, "n": r.n,
+                "status": r.status, "latency_us": r.latency_us, "d_bv": r.d_bv, "d_zeros": r.d_zeros}
+
+    def read(self, ticket: int):
+        import numpy as np
+        kind, n, sigma = self._keep[ticket]
+        L = wt_levels(sigma)
+        bv = np.zeros((L, wt_words_per_level(n)), dtype=np.uint64)
+        z = np.zeros(max(L, 1), dtype=np.uint64)
+        _check(lib().wt_server_read(self._h, ticket, ctypes.c_void_p(bv.ctypes.data),
+                                    ctypes.c_void_p(z.ctypes.data)), "wt_server_read")
+        return bv, (z[:L] if kind == WT_MATRIX else None)
+
+    def release(self, ticket: int):
+        _check(lib().wt_server_release(self._h, ticket), "wt_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        st = _native.WtServerStats()
+        _check(lib().wt_server_get_stats(self._h, ctypes.byref(st)), "wt_server_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if self._h:
+            lib().wt_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

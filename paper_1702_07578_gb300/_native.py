@@ -114,6 +114,10 @@ class WtServerStats(ctypes.Structure):
                 ("symbols_per_s", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t)]
 
 
+class WtProfile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_uint64 * 4)]
+
+
 # name -> (restype, argtypes); must cover every function of include/wt_gb300.h
 _C = ctypes
 SIGNATURES = {
@@ -135,8 +139,11 @@ SIGNATURES = {
     "wt_server_submit": (_C.c_int, [_C.c_void_p, _C.POINTER(WtRequest), _C.POINTER(_C.c_uint64)]),
     "wt_server_wait": (_C.c_int, [_C.c_void_p, _C.c_uint64, _C.c_int64, _C.POINTER(WtResult)]),
     "wt_server_release": (_C.c_int, [_C.c_void_p, _C.c_uint64]),
+    "wt_server_read": (_C.c_int, [_C.c_void_p, _C.c_uint64, _C.c_void_p, _C.c_void_p]),
     "wt_server_get_stats": (_C.c_int, [_C.c_void_p, _C.POINTER(WtServerStats)]),
     "wt_server_destroy": (None, [_C.c_void_p]),
+    "wt_profile_enable": (None, [_C.c_int]),
+    "wt_profile_read": (_C.c_int, [_C.POINTER(WtProfile), _C.c_int]),
 }
 
 

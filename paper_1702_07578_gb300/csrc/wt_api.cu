@@ -292,3 +292,93 @@ wt_status wt_build_batched(wt_kind kind, wt_symtype type, const wt_text_desc *h_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// diagnostics: CUDA events around kernel families
+
+namespace wtg {
+namespace {
+
+struct ProfRec {
+    cudaEvent_t begin, end;
+    int family;
+    uint32_t launches;
+};
+
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_pool;
+cudaEvent_t g_prof_open[4] = {};
+double g_prof_ms[4] = {};
+uint64_t g_prof_launches[4] = {};
+const uint32_t kFamilyLaunches[4] = {1, 1, 3, 2};
+
+cudaEvent_t take_event()
+{
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+}  // namespace
+
+bool profile_on() { return g_prof_on; }
+
+void profile_mark(int family, bool begin, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, s);
+    if (begin) {
+        g_prof_open[family] = e;
+    } else {
+        g_prof_recs.push_back(ProfRec{g_prof_open[family], e, family, kFamilyLaunches[family]});
+        g_prof_open[family] = nullptr;
+    }
+}
+
+}  // namespace wtg
+
+extern "C" {
+
+void wt_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(wtg::g_prof_mu);
+    wtg::g_prof_on = on != 0;
+}
+
+wt_status wt_profile_read(wt_profile *out, int reset)
+{
+    using namespace wtg;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_prof_recs) {
+        if (cudaEventSynchronize(r.end) != cudaSuccess) return WT_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.begin, r.end) != cudaSuccess) return WT_ERR_CUDA;
+        g_prof_ms[r.family] += ms;
+        g_prof_launches[r.family] += r.launches;
+        g_prof_pool.push_back(r.begin);
+        g_prof_pool.push_back(r.end);
+    }
+    g_prof_recs.clear();
+    if (out) {
+        for (int k = 0; k < 4; ++k) {
+            out->ms[k] = g_prof_ms[k];
+            out->launches[k] = g_prof_launches[k];
+        }
+    }
+    if (reset)
+        for (int k = 0; k < 4; ++k) {
+            g_prof_ms[k] = 0;
+            g_prof_launches[k] = 0;
+        }
+    return WT_OK;
+}
+
+}  // extern "C"

@@ -94,4 +94,8 @@ cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s
 
 cudaError_t configure_kernels();
 
+// Diagnostics: events around kernel families (see wt_profile in the header).
+void profile_mark(int family, bool begin, cudaStream_t s);
+bool profile_on();
+
 }  // namespace wtg

@@ -648,21 +648,28 @@ cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s
 cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s)
 {
     if (a.nslots == 0) return cudaSuccess;
+    const bool prof = profile_on();
     const bool root = a.round == 0 || a.kind == WT_MATRIX;
+    if (prof) profile_mark(3, true, s);
     if (root) k_root_jobs<<<(a.ntexts + 255) / 256, 256, 0, s>>>(a);
     else k_child_jobs<<<a.pnslots, 256, 0, s>>>(a);
     k_scan_groups<<<1, 1024, 0, s>>>(a);
+    if (prof) profile_mark(3, false, s);
     if (a.groups_ub == 0) return cudaGetLastError();
+    if (prof) profile_mark(1, true, s);
     k_hist<<<a.groups_ub, kThreads, 0, s>>>(a);
+    if (prof) { profile_mark(1, false, s); profile_mark(2, true, s); }
     k_blocksum<<<a.blocks_ub, 256, 0, s>>>(a);
     k_blockscan<<<1, 256, 0, s>>>(a);
     k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
+    if (prof) { profile_mark(2, false, s); profile_mark(0, true, s); }
     if (smem_width == 1)
         k_build<uint8_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint8_t>), s>>>(a);
     else if (smem_width == 2)
         k_build<uint16_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint16_t>), s>>>(a);
     else
         k_build<uint32_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint32_t>), s>>>(a);
+    if (prof) profile_mark(0, false, s);
     return cudaGetLastError();
 }
 

@@ -308,6 +308,31 @@ wt_status wt_server_wait(wt_server *s, uint64_t ticket, int64_t timeout_us, wt_r
     return r->status;
 }
 
+wt_status wt_server_read(wt_server *s, uint64_t ticket, uint64_t *h_bv, uint64_t *h_zeros)
+{
+    if (s == nullptr) return WT_ERR_INVALID_ARG;
+    std::shared_ptr<Req> r;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) return WT_ERR_NOT_FOUND;
+        r = it->second;
+        if (!r->done) return WT_ERR_BUSY;
+    }
+    const size_t bytes = (size_t)r->L * ((r->n + 63) / 64) * 8;
+    if (bytes && (h_bv == nullptr || r->d_bv == nullptr)) return WT_ERR_INVALID_ARG;
+    cudaSetDevice(s->cfg.device);
+    if (bytes && cudaMemcpy(h_bv, r->d_bv, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return WT_ERR_CUDA;
+    if (h_zeros && r->kind == WT_MATRIX) {
+        if (r->d_zeros) {
+            if (cudaMemcpy(h_zeros, r->d_zeros, r->L * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return WT_ERR_CUDA;
+        } else {
+            for (uint32_t l = 0; l < r->L; ++l) h_zeros[l] = 0;
+        }
+    }
+    return WT_OK;
+}
+
 wt_status wt_server_release(wt_server *s, uint64_t ticket)
 {
     if (s == nullptr) return WT_ERR_INVALID_ARG;

@@ -1,0 +1,88 @@
+"""Batched construction (wt_build_batched): every text bit-exact with the oracle
+and with a plain single-text build of the same text."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import gpu_wm, gpu_wt, to_u64, torch_text
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(specs, dtype):
+    texts = []
+    for n, sigma, seed in specs:
+        if sigma == 1:
+            texts.append(np.zeros(n, dtype))
+        else:
+            texts.append(synth.zipf_text(n, sigma, 0.8, seed, dtype))
+    return texts
+
+
+SPECS_MIXED = [(1000, 16, 1), (0, 256, 2), (70000, 256, 3), (1, 4096, 4), (300000, 4096, 5),
+               (65536, 65536, 6), (123457, 65536, 7), (5000, 1, 8), (64, 2, 9), (200001, 16, 10),
+               (131072, 257, 11), (777, 65536, 12)]
+
+
+@pytest.mark.parametrize("kind", ["wt", "wm"])
+def test_batched_matches_oracle_and_plain(kind):
+    import paper_1702_07578_gb300 as wtg
+    texts = _batch(SPECS_MIXED, np.uint16)
+    sigmas = [s for _, s, _ in SPECS_MIXED]
+    dts = [torch_text(t) for t in texts]
+    k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+    bvs, zs = wtg.wt_build_batched(k, dts, sigmas)
+    import torch
+    torch.cuda.synchronize()
+    for i, (T, sigma) in enumerate(zip(texts, sigmas)):
+        got = to_u64(bvs[i])
+        if kind == "wt":
+            exp = oracle.wt(T, sigma)
+            assert np.array_equal(got, exp), f"text {i}"
+            assert np.array_equal(got, gpu_wt(T, sigma)), f"text {i} vs plain"
+        else:
+            exp, ez = oracle.wm(T, sigma)
+            L = exp.shape[0]
+            assert np.array_equal(got, exp), f"text {i}"
+            assert np.array_equal(zs[i][:L].cpu().numpy().astype(np.uint64), ez), f"Z {i}"
+            pb, pz = gpu_wm(T, sigma)
+            assert np.array_equal(got, pb)
+
+
+@pytest.mark.parametrize("kind", ["wt", "wm"])
+def test_batched_workload_sample(kind):
+    """A slice of the 4096-text batched workload (log-uniform lengths, mixed sigma)."""
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    specs = synth.batch_specs(256, max_log=17)
+    texts = synth.batch_texts(specs)
+    sigmas = [s for _, s, _ in specs]
+    k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+    bvs, zs = wtg.wt_build_batched(k, [torch_text(t) for t in texts], sigmas)
+    torch.cuda.synchronize()
+    for i in range(0, len(texts), 7):
+        T, sigma = texts[i], sigmas[i]
+        if kind == "wt":
+            assert np.array_equal(to_u64(bvs[i]), oracle.wt(T, sigma)), f"text {i}"
+        else:
+            e, ez = oracle.wm(T, sigma)
+            assert np.array_equal(to_u64(bvs[i]), e), f"text {i}"
+            assert np.array_equal(zs[i][:e.shape[0]].cpu().numpy().astype(np.uint64), ez)
+
+
+def test_batched_symbol_range_error():
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    a = synth.uniform_text(5000, 100, 1, np.uint16)
+    b = synth.uniform_text(5000, 100, 2, np.uint16)
+    b[17] = 100
+    ts = [torch_text(a), torch_text(b)]
+    sz = wtg.wt_batched_workspace_size(wtg.WT_TREE, 2, [5000, 5000], [100, 100])
+    ws = torch.empty((sz,), dtype=torch.uint8, device="cuda")
+    wtg.wt_build_batched(wtg.WT_TREE, ts, [100, 100], ws=ws)
+    with pytest.raises(wtg.WtError) as e:
+        wtg.wt_sync_status(ws)
+    assert e.value.code == 2
