@@ -93,6 +93,35 @@ wt_status wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sig
  * this workspace during the last build on it (WT_OK if none), then clear it. */
 wt_status wt_sync_status(void *d_ws, void *stream);
 
+/* ---- wavelet tree without any device allocation --------------------------
+ * The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory: code running under a host
+ * framework that owns every device allocation, services that must keep a
+ * memory footprint fixed at start-up, or code paths that may not call
+ * cudaMalloc / cudaFree because those calls can synchronise the device.
+ *
+ * Same result as wt_build (bit-identical), but the workspace is a fixed
+ * array of 1 MiB in device memory inside this library, which every GPU that
+ * loads the library holds until the process exits.  The caller still passes the text and the output buffer.  The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Limit: texts whose workspace (wt_workspace_size(WT_TREE, ...)) exceeds the
+ * capacity are rejected with WT_ERR_OUT_OF_MEMORY before anything is
+ * launched.  With sigma <= 256 that allows about 16 million symbols; larger
+ * alphabets also need a re-sorted copy of the text (2 or 4 bytes per symbol)
+ * and allow far fewer.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and every call re-initialises what it reads from it, so
+ * calls are correct one after the other; two calls that overlap on the GPU
+ * (different streams, or different host threads) race on the array and give
+ * wrong results.  Errors the device would detect (a symbol >= sigma) are not
+ * reported by this call: such symbols give unspecified bit vectors (the
+ * kernels still write only inside d_bv). */
+wt_status wt_build_static_ws(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                             uint64_t *d_bv, void *stream);
+
 /* ---- batched construction ---------------------------------------------
  * Many independent texts built together (all WT or all WM, one storage
  * type).  Each descriptor names its device text, length, alphabet and

@@ -142,6 +142,8 @@ SIGNATURES = {
     "wt_server_read": (_C.c_int, [_C.c_void_p, _C.c_uint64, _C.c_void_p, _C.c_void_p]),
     "wt_server_get_stats": (_C.c_int, [_C.c_void_p, _C.POINTER(WtServerStats)]),
     "wt_server_destroy": (None, [_C.c_void_p]),
+    "wt_build_static_ws": (_C.c_int, [_C.c_void_p, _C.c_int, _C.c_uint64, _C.c_uint64,
+                                      _C.c_void_p, _C.c_void_p]),
     "wt_profile_enable": (None, [_C.c_int]),
     "wt_profile_read": (_C.c_int, [_C.POINTER(WtProfile), _C.c_int]),
 }

@@ -382,3 +382,52 @@ wt_status wt_profile_read(wt_profile *out, int reset)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Wavelet tree build that allocates nothing (see wt_build_static_ws in the
+// header).  Its scratch is a fixed array in device memory, so callers that are
+// not allowed to allocate device memory can still build small texts.
+
+namespace wtg {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;   // 1 MiB per device
+
+// One copy per device that loads this library; it lives until the process exits.
+__device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void *g_static_ptr[64] = {};
+
+// Device address of g_static_scratch on the current device (looked up once per device).
+wt_status static_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WT_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (g_static_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return WT_ERR_CUDA;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return WT_OK;
+}
+
+}  // namespace
+}  // namespace wtg
+
+extern "C" wt_status wt_build_static_ws(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                                        uint64_t *d_bv, void *stream)
+{
+    using namespace wtg;
+    HostText h{d_text, n, sigma, d_bv, nullptr};
+    Plan p;
+    wt_status st = make_plan(WT_TREE, type, &h, 1, true, p);
+    if (st != WT_OK) return st;
+    if (p.bytes > kStaticScratchBytes) return WT_ERR_OUT_OF_MEMORY;
+    void *ws = nullptr;
+    st = static_scratch(&ws);
+    if (st != WT_OK) return st;
+    return run_plan(WT_TREE, p, ws, kStaticScratchBytes, static_cast<cudaStream_t>(stream));
+}
