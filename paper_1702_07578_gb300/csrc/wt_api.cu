@@ -190,6 +190,11 @@ wt_status run_plan(wt_kind kind, Plan &p, void *d_ws, size_t ws_bytes, cudaStrea
         a.gelems = (uint32_t)group_elems(p.width[r]);
         a.groups_ub = p.groups_ub[r];
         a.blocks_ub = p.blocks_ub[r];
+        for (uint32_t i = 0; i < p.count; ++i) {
+            const TextInfo &ti = p.texts[i];
+            if (ti.nslots[r] == 0) continue;
+            if (ti.L - kChunk * r > (uint32_t)kChunk) a.any_cut = 1; else a.any_plain = 1;
+        }
         if (launch_round(a, p.width[r], s) != cudaSuccess) return WT_ERR_CUDA;
     }
     return WT_OK;
@@ -330,7 +335,7 @@ cudaEvent_t take_event()
 
 bool profile_on() { return g_prof_on; }
 
-void profile_mark(int family, bool begin, cudaStream_t s)
+void profile_mark(int family, bool begin, cudaStream_t s, uint32_t launches)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEvent_t e = take_event();
@@ -338,7 +343,7 @@ void profile_mark(int family, bool begin, cudaStream_t s)
     if (begin) {
         g_prof_open[family] = e;
     } else {
-        g_prof_recs.push_back(ProfRec{g_prof_open[family], e, family, kFamilyLaunches[family]});
+        g_prof_recs.push_back(ProfRec{g_prof_open[family], e, family, launches ? launches : kFamilyLaunches[family]});
         g_prof_open[family] = nullptr;
     }
 }

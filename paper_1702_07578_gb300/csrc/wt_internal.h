@@ -84,6 +84,8 @@ struct RoundArgs {
     uint32_t gelems;         // symbols per group in this round
     uint32_t groups_ub;      // grid bound for per-group kernels
     uint32_t blocks_ub;      // grid bound for per-block kernels
+    uint32_t any_cut;        // some job of the round writes a re-sorted text (k_build)
+    uint32_t any_plain;      // some job of the round has no cut (k_build_bs)
 };
 
 // Launches one round on the stream.  Returns a CUDA error code.
@@ -95,7 +97,7 @@ cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s
 cudaError_t configure_kernels();
 
 // Diagnostics: events around kernel families (see wt_profile in the header).
-void profile_mark(int family, bool begin, cudaStream_t s);
+void profile_mark(int family, bool begin, cudaStream_t s, uint32_t launches = 0);
 bool profile_on();
 
 }  // namespace wtg

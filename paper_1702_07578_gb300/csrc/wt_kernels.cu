@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build(RoundArgs a)
     const uint32_t gi = g - jb.g0;
     const bool matrix = a.kind == WT_MATRIX;
     const bool has_cut = rt.cut != nullptr;
+    if (!has_cut) return;                            // rounds without a cut: k_build_bs
 
     // job totals -> per-level class totals and interval starts (fold, Alg. 1;
     // zero-based prefix sum in id or pi_l order, Sec. 3.1 / 5.1)
@@ -624,10 +625,352 @@ __global__ void __launch_bounds__(kThreads, 2) k_build(RoundArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Bit-sliced variant of a2-a4 for rounds without a cut (every text with sigma
+// <= 256, and the last round of larger alphabets).  Thread t of the block owns
+// word t of every bit plane of the tile: bit e of plane k is bit k (from the
+// most significant of the round's code bits) of symbol 32t + e.  The stable
+// split of the tile by plane l (Sec. 5: zeros keep their order, then ones) is
+// then, for each word, a compress of every later plane to the zero and to the
+// one positions of plane l (Hacker's Delight, "compress"), placed at the word's
+// exclusive zero count and at Z + its exclusive one count.
+
+namespace {
+
+constexpr int kBsWords = kThreads;            // words per plane = symbols / 32
+constexpr int kBsTile = kBsWords * 32;        // 16384 symbols per tile
+
+struct BsSmem {
+    uint32_t plane[2][kChunk][kBsWords + 1];  // current / next planes (+1 word of overflow)
+    uint32_t lvl[kBsWords + 4];               // the current level's plane, tile order
+    uint32_t zoff[kBsWords + 1];              // exclusive zero count before each word
+    uint32_t wsum[kWarps];
+    uint32_t offq[kCols];
+    uint32_t jP[kCols + 1];
+    uint32_t oP[kCols + 1];
+    uint32_t jcnt[kHeap];
+    uint32_t jspos[kHeap];
+    uint32_t cnt[kHeap];
+    uint32_t loc[kHeap];
+    uint32_t glo[kHeap];
+    uint32_t wpre[kHeap];
+    uint32_t wtot[kChunk + 2];
+};
+
+// Move vectors of compress(., m) (Hacker's Delight, Sec. 7-4): five masks that
+// say which bits travel 1, 2, 4, 8 and 16 places towards bit 0.
+__device__ __forceinline__ void compress_moves(uint32_t m, uint32_t mv[5])
+{
+    uint32_t mk = ~m << 1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        uint32_t mp = mk ^ (mk << 1);
+        mp ^= mp << 2;
+        mp ^= mp << 4;
+        mp ^= mp << 8;
+        mp ^= mp << 16;
+        const uint32_t v = mp & m;
+        m = (m ^ v) | (v >> (1 << i));
+        mv[i] = v;
+        mk &= ~mp;
+    }
+}
+
+__device__ __forceinline__ uint32_t compress_apply(uint32_t x, uint32_t m, const uint32_t mv[5])
+{
+    x &= m;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const uint32_t t = x & mv[i];
+        x = (x ^ t) | (t >> (1 << i));
+    }
+    return x;
+}
+
+// OR `len` bits of `part` into a plane at bit offset d (shared memory).
+__device__ __forceinline__ void place_bits(uint32_t *plane, uint32_t d, uint32_t part, uint32_t len)
+{
+    if (len == 0) return;
+    const uint32_t w = d >> 5, s = d & 31u;
+    atomicOr(plane + w, part << s);
+    if (s + len > 32u) atomicOr(plane + w + 1, part >> (32u - s));
+}
+
+// 8x8 bit transpose of the bytes of (lo, hi): afterwards byte j holds bit j of
+// input byte i at bit i.
+__device__ __forceinline__ void transpose8(uint32_t &lo, uint32_t &hi)
+{
+    uint32_t t;
+    t = (lo ^ (lo >> 7)) & 0x00AA00AAu; lo = lo ^ t ^ (t << 7);
+    t = (hi ^ (hi >> 7)) & 0x00AA00AAu; hi = hi ^ t ^ (t << 7);
+    t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo = lo ^ t ^ (t << 14);
+    t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi = hi ^ t ^ (t << 14);
+    t = (lo ^ (hi << 4)) & 0xF0F0F0F0u; lo = lo ^ t; hi = hi ^ (t >> 4);
+}
+
+// Low byte of each of 4 consecutive symbols of width w, packed into one word.
+__device__ __forceinline__ uint32_t pack4(const uint4 &v, int half, uint32_t w)
+{
+    if (w == 2) {
+        const uint32_t a = half ? v.z : v.x, b = half ? v.w : v.y;
+        return __byte_perm(a, b, 0x6420);
+    }
+    // w == 4: four symbols in v
+    return __byte_perm(__byte_perm(v.x, v.y, 0x0040), __byte_perm(v.z, v.w, 0x0040), 0x5410);
+}
+
+// Thread t's 32 symbols [32t, 32t + 32) of the tile as 8 words of 4 bytes (the
+// low byte of each symbol); symbols at or beyond m read as 0xff (all ones, so
+// padding stays at the end of every stable split).
+__device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t m, uint32_t x[8])
+{
+    const uint32_t e0 = threadIdx.x * 32u;
+    const uint8_t *p = tile + (size_t)e0 * w;
+    if (e0 + 32u <= m && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+        if (w == 1) {
+            const uint4 a = __ldg(q), b = __ldg(q + 1);
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else if (w == 2) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint4 a = __ldg(q + k);
+                x[2 * k] = pack4(a, 0, 2);
+                x[2 * k + 1] = pack4(a, 1, 2);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = pack4(__ldg(q + k), 0, 4);
+        }
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t e = e0 + 4u * k + b;
+            const uint32_t v = e < m ? (load_sym(tile, w, e) & 0xffu) : 0xffu;
+            word |= v << (8 * b);
+        }
+        x[k] = word;
+    }
+}
+
+// Exclusive prefix of one value per thread over the block; returns it and
+// writes the block total to *total (every thread).  Uses wsum, one barrier.
+__device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t *wsum, uint32_t *total)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, d);
+        if (lane >= (uint32_t)d) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    const uint32_t ws = lane < (uint32_t)kWarps ? wsum[lane] : 0u;
+    uint32_t before = (lane < warp) ? ws : 0u, all = ws;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        before += __shfl_xor_sync(kFull, before, d);
+        all += __shfl_xor_sync(kFull, all, d);
+    }
+    *total = all;
+    return before + inc - v;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    BsSmem &sm = *reinterpret_cast<BsSmem *>(smem_raw);
+
+    const uint32_t g = blockIdx.x;
+    if (g >= a.ctl->total_groups[a.round]) return;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t slot = find_slot(a.jobs, a.nslots, g);
+    const Job jb = a.jobs[slot];
+    const TextInfo &t = a.texts[jb.text];
+    const RoundText rt = round_text(t, a.round);
+    if (rt.cut != nullptr) return;                   // rounds with a cut: k_build
+    const uint32_t h = rt.h, rb = rt.rb;             // rb == h here
+    const uint32_t gi = g - jb.g0;
+    const bool matrix = a.kind == WT_MATRIX;
+
+    // job totals -> class totals and interval starts of every level
+    for (uint32_t q = tid; q < kCols; q += kThreads) {
+        sm.cnt[q] = a.jobhist[(size_t)slot * kCols + q];      // scratch for the scan below
+        sm.offq[q] = a.gexcl[(size_t)g * kCols + q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.cnt[i]; }, [](uint32_t i) { return i; },
+                                     [&](uint32_t i, uint32_t v) { sm.jP[i] = v; });
+        if (lane == 0) sm.jP[256] = tot;
+    }
+    __syncthreads();
+    for (uint32_t idx = tid; idx < kHeap; idx += kThreads) {
+        if (idx == 0) continue;
+        const uint32_t l = 31u - __clz(idx), q = idx - (1u << l);
+        if (l <= h) sm.jcnt[idx] = sm.jP[(q + 1) << (h - l)] - sm.jP[q << (h - l)];
+    }
+    __syncthreads();
+    if (warp <= h) {
+        const uint32_t l = warp, base = 1u << l;
+        warp_scan_256(base, [&](uint32_t q) { return sm.jcnt[base + q]; },
+                      [&](uint32_t i) { return matrix ? rev_bits(i, l) : i; },
+                      [&](uint32_t q, uint32_t v) { sm.jspos[base + q] = v; });
+    }
+    if (matrix && gi == 0 && tid < h) {
+        const uint32_t l = tid, base = 2u << l;
+        uint32_t z = 0;
+        for (uint32_t p = 0; p < base; p += 2) z += sm.jcnt[base + p];
+        t.zeros[rt.c + l] = z;
+    }
+    __syncthreads();
+
+    const uint64_t g_begin = (uint64_t)gi * a.gelems;
+    const uint64_t g_end = min((uint64_t)jb.n, g_begin + a.gelems);
+    const uint8_t *in_base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
+
+    for (uint64_t t0 = g_begin; t0 < g_end; t0 += kBsTile) {
+        const uint32_t m = (uint32_t)min((uint64_t)kBsTile, g_end - t0);
+        // ---- clear the plane buffers; prefix of the job offsets of this tile
+        for (uint32_t i = tid; i < 2 * kChunk * (kBsWords + 1); i += kThreads) (&sm.plane[0][0][0])[i] = 0;
+        if (warp == 1) {
+            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.offq[i]; }, [](uint32_t i) { return i; },
+                                         [&](uint32_t i, uint32_t v) { sm.oP[i] = v; });
+            if (lane == 0) sm.oP[256] = tot;
+        }
+        if (tid == 0) sm.cnt[1] = m;                 // level 0: one class, the whole tile
+        __syncthreads();
+        // ---- load and transpose: plane k = code bit rb-1-k of every symbol
+        {
+            uint32_t x[8];
+            load32(in_base + (size_t)t0 * rt.in_w, rt.in_w, m, x);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) transpose8(x[2 * b], x[2 * b + 1]);
+            for (uint32_t k = 0; k < h; ++k) {
+                const uint32_t j = rb - 1u - k;               // bit position inside the byte
+                const uint32_t sel = (j & 3u) | ((j & 3u) + 4u) << 4;
+                const bool hi = j >= 4u;                      // hi half of each 8-symbol block
+                const uint32_t t01 = __byte_perm(hi ? x[1] : x[0], hi ? x[3] : x[2], sel);
+                const uint32_t t23 = __byte_perm(hi ? x[5] : x[4], hi ? x[7] : x[6], sel);
+                sm.plane[0][k][tid] = __byte_perm(t01, t23, 0x5410);
+            }
+        }
+        __syncthreads();
+
+        for (uint32_t l = 0; l < h; ++l) {
+            uint32_t(*cur)[kBsWords + 1] = sm.plane[l & 1];
+            uint32_t(*nxt)[kBsWords + 1] = sm.plane[(l + 1) & 1];
+            const uint32_t base = 1u << l;
+            // tables of level l: class starts in tile order (reversed prefixes),
+            // interval starts in the level, destination words
+            if (warp == 0) {
+                warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
+                              [&](uint32_t i) { return rev_bits(i, l); },
+                              [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
+            } else if (warp == 1) {
+                const uint32_t s = h - l;
+                const uint32_t wt = warp_scan_256(
+                    base,
+                    [&](uint32_t q) {
+                        const uint32_t c = sm.cnt[base + q];
+                        const uint32_t gs = jb.off + sm.jspos[base + q] + (sm.oP[(q + 1) << s] - sm.oP[q << s]);
+                        sm.glo[base + q] = gs;
+                        if (c == 0) return 0u;
+                        return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
+                    },
+                    [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
+                if (lane == 0) sm.wtot[l] = wt;
+            }
+            const uint32_t mword = cur[l][tid];
+            sm.lvl[tid] = mword;
+            uint32_t zt;
+            const uint32_t zo = block_excl(__popc(~mword), sm.wsum, &zt);   // barrier inside
+            sm.zoff[tid] = zo;
+            if (tid == 0) sm.zoff[kBsWords] = zt;
+            __syncthreads();
+
+            // copy every class's bits to its interval start in level c + l
+            {
+                const uint32_t wt = sm.wtot[l];
+                uint64_t *lv = t.bv + (uint64_t)(rt.c + l) * t.W;
+                for (uint32_t k = tid; k < wt; k += kThreads) {
+                    uint32_t lo = 0, hi = base;
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (sm.wpre[base + mid] <= k) lo = mid; else hi = mid;
+                    }
+                    const uint32_t idx = base + lo;
+                    const uint64_t gs = sm.glo[idx], ge = gs + sm.cnt[idx];
+                    const uint64_t word = (gs >> 6) + (k - sm.wpre[idx]);
+                    const uint64_t wb = word << 6;
+                    const uint32_t blo = (uint32_t)((gs > wb ? gs : wb) - wb);
+                    uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
+                    const uint32_t src = sm.loc[idx] + (uint32_t)(wb + blo - gs);
+                    const uint64_t val = extract_bits(sm.lvl, src, bhi - blo) << blo;
+                    if (ge == t.n) bhi = 64;
+                    if (blo == 0 && bhi == 64) {
+                        lv[word] = val;
+                    } else {
+                        const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
+                        atomicAnd(reinterpret_cast<unsigned long long *>(lv + word), ~msk);
+                        atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
+                    }
+                }
+            }
+
+            // class counts of level l + 1: each class splits into its zeros and ones
+            for (uint32_t q = tid; q < base; q += kThreads) {
+                const uint32_t c = sm.cnt[base + q];
+                const uint32_t s0 = sm.loc[base + q], s1 = s0 + c;
+                auto ones_before = [&](uint32_t p) {
+                    const uint32_t w = p >> 5, r = p & 31u;
+                    uint32_t o = w * 32u - sm.zoff[w];
+                    if (r) o += __popc(sm.lvl[w] & ((1u << r) - 1u));
+                    return o;
+                };
+                const uint32_t ones = ones_before(s1) - ones_before(s0);
+                sm.cnt[2 * base + 2 * q] = c - ones;
+                sm.cnt[2 * base + 2 * q + 1] = ones;
+            }
+
+            // stable split of every later plane by plane l
+            if (l + 1 < h) {
+                uint32_t mz[5], mo[5];
+                compress_moves(~mword, mz);
+                compress_moves(mword, mo);
+                const uint32_t nz = 32u - __popc(mword);
+                const uint32_t dz = zo, d1 = zt + tid * 32u - zo;
+                for (uint32_t k = l + 1; k < h; ++k) {
+                    const uint32_t x = cur[k][tid];
+                    place_bits(nxt[k], dz, compress_apply(x, ~mword, mz), nz);
+                    place_bits(nxt[k], d1, compress_apply(x, mword, mo), 32u - nz);
+                    cur[k][tid] = 0;
+                }
+                if (tid == 0)
+                    for (uint32_t k = l + 1; k < h; ++k) cur[k][kBsWords] = 0;
+            }
+            __syncthreads();
+        }
+        // leaf counts of this tile advance the job offsets for the next tile
+        for (uint32_t q = tid; q < (1u << h); q += kThreads) sm.offq[q] += sm.cnt[(1u << h) + q];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 
 cudaError_t configure_kernels()
 {
     cudaError_t e;
+    e = cudaFuncSetAttribute(k_build_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_build<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(BuildSmem<uint8_t>));
     if (e != cudaSuccess) return e;
@@ -663,13 +1006,19 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     k_blockscan<<<1, 256, 0, s>>>(a);
     k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
     if (prof) { profile_mark(2, false, s); profile_mark(0, true, s); }
+    if (a.any_plain)
+        k_build_bs<<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    if (!a.any_cut) {
+        if (prof) profile_mark(0, false, s, 1);
+        return cudaGetLastError();
+    }
     if (smem_width == 1)
         k_build<uint8_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint8_t>), s>>>(a);
     else if (smem_width == 2)
         k_build<uint16_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint16_t>), s>>>(a);
     else
         k_build<uint32_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint32_t>), s>>>(a);
-    if (prof) profile_mark(0, false, s);
+    if (prof) profile_mark(0, false, s, a.any_plain ? 2 : 1);
     return cudaGetLastError();
 }
 
