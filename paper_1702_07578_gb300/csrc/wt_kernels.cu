@@ -626,38 +626,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_build(RoundArgs a)
 
 // ---------------------------------------------------------------------------
 // Bit-sliced variant of a2-a4 for rounds without a cut (every text with sigma
-// <= 256, and the last round of larger alphabets).  Thread t of the block owns
-// word t of every bit plane of the tile: bit e of plane k is bit k (from the
-// most significant of the round's code bits) of symbol 32t + e.  The stable
-// split of the tile by plane l (Sec. 5: zeros keep their order, then ones) is
-// then, for each word, a compress of every later plane to the zero and to the
-// one positions of plane l (Hacker's Delight, "compress"), placed at the word's
-// exclusive zero count and at Z + its exclusive one count.
+// <= 256, and the last round of larger alphabets).  The tile is held as bit
+// planes: bit e of word w of plane k is bit k (counted from the most significant
+// of the round's code bits) of symbol 32w + e.  Thread t owns words 2t and
+// 2t + 1.  The stable split of the tile by plane l (zeros keep their order,
+// then ones; Sec. 5) is, for each word, a compress of every later plane to the
+// zero positions and to the one positions of plane l (Hacker's Delight,
+// "compress"), placed at the word's exclusive zero count and at Z plus its
+// exclusive one count.  Plane l itself, in that order, is level l.
 
 namespace {
 
-constexpr int kBsWords = kThreads;            // words per plane = symbols / 32
-constexpr int kBsTile = kBsWords * 32;        // 16384 symbols per tile
+constexpr int kBsWords = 2 * kThreads;        // words per plane
+constexpr int kBsTile = kBsWords * 32;        // 32768 symbols per tile
 
 struct BsSmem {
-    uint32_t plane[2][kChunk][kBsWords + 1];  // current / next planes (+1 word of overflow)
+    uint32_t plane[2][kChunk][kBsWords + 2];  // current / next planes (+ overflow words)
     uint32_t lvl[kBsWords + 4];               // the current level's plane, tile order
-    uint32_t zoff[kBsWords + 1];              // exclusive zero count before each word
-    uint32_t wsum[kWarps];
-    uint32_t offq[kCols];
+    uint32_t zloc[kBsWords];                  // zeros before each word inside its warp's range
+    uint32_t wsum[kWarps];                    // zeros of each warp's range
+    uint32_t offq[kCols];                     // class counts of the job before this tile
     uint32_t jP[kCols + 1];
     uint32_t oP[kCols + 1];
-    uint32_t jcnt[kHeap];
-    uint32_t jspos[kHeap];
-    uint32_t cnt[kHeap];
-    uint32_t loc[kHeap];
-    uint32_t glo[kHeap];
-    uint32_t wpre[kHeap];
+    uint32_t jcnt[kHeap];                     // job class totals per level
+    uint32_t jspos[kHeap];                    // interval starts inside the job per level
+    uint32_t cnt[kHeap];                      // tile class counts per level
+    uint32_t loc[kHeap];                      // class start in tile order per level
+    uint32_t glo[kHeap];                      // class start inside the text's level (bits)
+    uint32_t wpre[kHeap];                     // destination words before each class
     uint32_t wtot[kChunk + 2];
 };
 
-// Move vectors of compress(., m) (Hacker's Delight, Sec. 7-4): five masks that
-// say which bits travel 1, 2, 4, 8 and 16 places towards bit 0.
+// Move vectors of compress(., m) (Hacker's Delight, Sec. 7-4): the bits that
+// travel 1, 2, 4, 8 and 16 places towards bit 0 in the five rounds.
 __device__ __forceinline__ void compress_moves(uint32_t m, uint32_t mv[5])
 {
     uint32_t mk = ~m << 1;
@@ -686,13 +687,15 @@ __device__ __forceinline__ uint32_t compress_apply(uint32_t x, uint32_t m, const
     return x;
 }
 
-// OR `len` bits of `part` into a plane at bit offset d (shared memory).
-__device__ __forceinline__ void place_bits(uint32_t *plane, uint32_t d, uint32_t part, uint32_t len)
+// OR the low `len` (<= 64) bits of `part` into a plane at bit offset d.
+__device__ __forceinline__ void place_bits(uint32_t *plane, uint32_t d, uint64_t part, uint32_t len)
 {
     if (len == 0) return;
     const uint32_t w = d >> 5, s = d & 31u;
-    atomicOr(plane + w, part << s);
-    if (s + len > 32u) atomicOr(plane + w + 1, part >> (32u - s));
+    const uint64_t lo = part << s;
+    atomicOr(plane + w, (uint32_t)lo);
+    if (s + len > 32u) atomicOr(plane + w + 1, (uint32_t)(lo >> 32));
+    if (s + len > 64u) atomicOr(plane + w + 2, (uint32_t)(part >> (64u - s)));
 }
 
 // 8x8 bit transpose of the bytes of (lo, hi): afterwards byte j holds bit j of
@@ -707,23 +710,21 @@ __device__ __forceinline__ void transpose8(uint32_t &lo, uint32_t &hi)
     t = (lo ^ (hi << 4)) & 0xF0F0F0F0u; lo = lo ^ t; hi = hi ^ (t >> 4);
 }
 
-// Low byte of each of 4 consecutive symbols of width w, packed into one word.
+// Low bytes of 4 consecutive symbols of width w (2 or 4) packed into one word.
 __device__ __forceinline__ uint32_t pack4(const uint4 &v, int half, uint32_t w)
 {
     if (w == 2) {
         const uint32_t a = half ? v.z : v.x, b = half ? v.w : v.y;
         return __byte_perm(a, b, 0x6420);
     }
-    // w == 4: four symbols in v
     return __byte_perm(__byte_perm(v.x, v.y, 0x0040), __byte_perm(v.z, v.w, 0x0040), 0x5410);
 }
 
-// Thread t's 32 symbols [32t, 32t + 32) of the tile as 8 words of 4 bytes (the
-// low byte of each symbol); symbols at or beyond m read as 0xff (all ones, so
-// padding stays at the end of every stable split).
-__device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t m, uint32_t x[8])
+// Symbols [e0, e0 + 32) of the tile as 8 words of 4 bytes (the low byte of each
+// symbol); symbols at or beyond m read as 0xff, all ones, so that padding stays
+// at the end of every stable split.
+__device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t e0, uint32_t m, uint32_t x[8])
 {
-    const uint32_t e0 = threadIdx.x * 32u;
     const uint8_t *p = tile + (size_t)e0 * w;
     if (e0 + 32u <= m && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
         const uint4 *q = reinterpret_cast<const uint4 *>(p);
@@ -757,28 +758,20 @@ __device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t
     }
 }
 
-// Exclusive prefix of one value per thread over the block; returns it and
-// writes the block total to *total (every thread).  Uses wsum, one barrier.
-__device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t *wsum, uint32_t *total)
+// Transposes 32 symbols and stores plane k (code bit rb-1-k) of word w.
+__device__ __forceinline__ void store_planes(uint32_t x[8], uint32_t rb, uint32_t h,
+                                             uint32_t (*planes)[kBsWords + 2], uint32_t w)
 {
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint32_t inc = v;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, inc, d);
-        if (lane >= (uint32_t)d) inc += y;
+    for (int b = 0; b < 4; ++b) transpose8(x[2 * b], x[2 * b + 1]);
+    for (uint32_t k = 0; k < h; ++k) {
+        const uint32_t j = rb - 1u - k;               // bit position inside the byte
+        const uint32_t sel = (j & 3u) | ((j & 3u) + 4u) << 4;
+        const bool hi = j >= 4u;
+        const uint32_t t01 = __byte_perm(hi ? x[1] : x[0], hi ? x[3] : x[2], sel);
+        const uint32_t t23 = __byte_perm(hi ? x[5] : x[4], hi ? x[7] : x[6], sel);
+        planes[k][w] = __byte_perm(t01, t23, 0x5410);
     }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    const uint32_t ws = lane < (uint32_t)kWarps ? wsum[lane] : 0u;
-    uint32_t before = (lane < warp) ? ws : 0u, all = ws;
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-        before += __shfl_xor_sync(kFull, before, d);
-        all += __shfl_xor_sync(kFull, all, d);
-    }
-    *total = all;
-    return before + inc - v;
 }
 
 }  // namespace
@@ -800,7 +793,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const uint32_t gi = g - jb.g0;
     const bool matrix = a.kind == WT_MATRIX;
 
-    // job totals -> class totals and interval starts of every level
+    // job totals -> class totals and interval starts of every level (fold,
+    // Alg. 1; zero-based prefix sums in id or pi_l order, Sec. 3.1 / 5.1)
     for (uint32_t q = tid; q < kCols; q += kThreads) {
         sm.cnt[q] = a.jobhist[(size_t)slot * kCols + q];      // scratch for the scan below
         sm.offq[q] = a.gexcl[(size_t)g * kCols + q];
@@ -824,7 +818,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                       [&](uint32_t i) { return matrix ? rev_bits(i, l) : i; },
                       [&](uint32_t q, uint32_t v) { sm.jspos[base + q] = v; });
     }
-    if (matrix && gi == 0 && tid < h) {
+    if (matrix && gi == 0 && tid < h) {              // Z[c + l]: even (l+1)-prefixes
         const uint32_t l = tid, base = 2u << l;
         uint32_t z = 0;
         for (uint32_t p = 0; p < base; p += 2) z += sm.jcnt[base + p];
@@ -835,73 +829,125 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const uint64_t g_begin = (uint64_t)gi * a.gelems;
     const uint64_t g_end = min((uint64_t)jb.n, g_begin + a.gelems);
     const uint8_t *in_base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
+    const uint32_t w0 = 2u * tid;                    // this thread's words: w0, w0 + 1
+
+    // Class tables of level l (counts already in cnt): tile-order starts
+    // (reversed prefixes), interval starts in the level, destination words.
+    // Run by one warp.
+    auto level_tables = [&](uint32_t l) {
+        const uint32_t base = 1u << l, s = h - l;
+        warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
+                      [&](uint32_t i) { return rev_bits(i, l); },
+                      [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
+        const uint32_t wt = warp_scan_256(
+            base,
+            [&](uint32_t q) {
+                const uint32_t c = sm.cnt[base + q];
+                const uint32_t gs = jb.off + sm.jspos[base + q] + (sm.oP[(q + 1) << s] - sm.oP[q << s]);
+                sm.glo[base + q] = gs;
+                if (c == 0) return 0u;
+                return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
+            },
+            [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
+        if (lane == 0) sm.wtot[l] = wt;
+    };
 
     for (uint64_t t0 = g_begin; t0 < g_end; t0 += kBsTile) {
         const uint32_t m = (uint32_t)min((uint64_t)kBsTile, g_end - t0);
-        // ---- clear the plane buffers; prefix of the job offsets of this tile
-        for (uint32_t i = tid; i < 2 * kChunk * (kBsWords + 1); i += kThreads) (&sm.plane[0][0][0])[i] = 0;
-        if (warp == 1) {
+        // ---- clear the plane buffers; job offsets before this tile; level-0 tables
+        for (uint32_t i = tid; i < 2 * kChunk * (kBsWords + 2); i += kThreads) (&sm.plane[0][0][0])[i] = 0;
+        if (warp == 0) {
             uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.offq[i]; }, [](uint32_t i) { return i; },
                                          [&](uint32_t i, uint32_t v) { sm.oP[i] = v; });
             if (lane == 0) sm.oP[256] = tot;
+            if (lane == 0) sm.cnt[1] = m;
+            __syncwarp();
+            level_tables(0);
         }
-        if (tid == 0) sm.cnt[1] = m;                 // level 0: one class, the whole tile
         __syncthreads();
-        // ---- load and transpose: plane k = code bit rb-1-k of every symbol
+        // ---- load and transpose: plane k holds code bit rb-1-k of every symbol
         {
+            const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             uint32_t x[8];
-            load32(in_base + (size_t)t0 * rt.in_w, rt.in_w, m, x);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) transpose8(x[2 * b], x[2 * b + 1]);
-            for (uint32_t k = 0; k < h; ++k) {
-                const uint32_t j = rb - 1u - k;               // bit position inside the byte
-                const uint32_t sel = (j & 3u) | ((j & 3u) + 4u) << 4;
-                const bool hi = j >= 4u;                      // hi half of each 8-symbol block
-                const uint32_t t01 = __byte_perm(hi ? x[1] : x[0], hi ? x[3] : x[2], sel);
-                const uint32_t t23 = __byte_perm(hi ? x[5] : x[4], hi ? x[7] : x[6], sel);
-                sm.plane[0][k][tid] = __byte_perm(t01, t23, 0x5410);
-            }
+            load32(tile, rt.in_w, 32u * w0, m, x);
+            store_planes(x, rb, h, sm.plane[0], w0);
+            load32(tile, rt.in_w, 32u * w0 + 32u, m, x);
+            store_planes(x, rb, h, sm.plane[0], w0 + 1);
         }
         __syncthreads();
 
         for (uint32_t l = 0; l < h; ++l) {
-            uint32_t(*cur)[kBsWords + 1] = sm.plane[l & 1];
-            uint32_t(*nxt)[kBsWords + 1] = sm.plane[(l + 1) & 1];
+            uint32_t(*cur)[kBsWords + 2] = sm.plane[l & 1];
+            uint32_t(*nxt)[kBsWords + 2] = sm.plane[(l + 1) & 1];
             const uint32_t base = 1u << l;
-            // tables of level l: class starts in tile order (reversed prefixes),
-            // interval starts in the level, destination words
-            if (warp == 0) {
-                warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
-                              [&](uint32_t i) { return rev_bits(i, l); },
-                              [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
-            } else if (warp == 1) {
-                const uint32_t s = h - l;
-                const uint32_t wt = warp_scan_256(
-                    base,
-                    [&](uint32_t q) {
-                        const uint32_t c = sm.cnt[base + q];
-                        const uint32_t gs = jb.off + sm.jspos[base + q] + (sm.oP[(q + 1) << s] - sm.oP[q << s]);
-                        sm.glo[base + q] = gs;
-                        if (c == 0) return 0u;
-                        return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
-                    },
-                    [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
-                if (lane == 0) sm.wtot[l] = wt;
+            // plane l in tile order is level l; zero counts of this thread's words
+            const uint32_t m0 = cur[l][w0], m1 = cur[l][w0 + 1];
+            sm.lvl[w0] = m0;
+            sm.lvl[w0 + 1] = m1;
+            const uint32_t z0 = __popc(~m0), z1 = __popc(~m1);
+            uint32_t inc = z0 + z1;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                if (lane >= (uint32_t)d) inc += y;
             }
-            const uint32_t mword = cur[l][tid];
-            sm.lvl[tid] = mword;
-            uint32_t zt;
-            const uint32_t zo = block_excl(__popc(~mword), sm.wsum, &zt);   // barrier inside
-            sm.zoff[tid] = zo;
-            if (tid == 0) sm.zoff[kBsWords] = zt;
+            const uint32_t zl = inc - z0 - z1;             // zeros before word w0 inside the warp
+            sm.zloc[w0] = zl;
+            sm.zloc[w0 + 1] = zl + z0;
+            if (lane == 31) sm.wsum[warp] = inc;
             __syncthreads();
+            // zeros before each warp's range; total zeros Z of the tile
+            const uint32_t ws = lane < (uint32_t)kWarps ? sm.wsum[lane] : 0u;
+            uint32_t wex = ws;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, wex, d);
+                if (lane >= (uint32_t)d) wex += y;
+            }
+            const uint32_t zt = __shfl_sync(kFull, wex, 31);
+            wex -= ws;                                      // lane j: zeros before warp j's words
+            const uint32_t zo = __shfl_sync(kFull, wex, warp) + zl;
+
+            if (warp == 0) {
+                // class counts of level l + 1: each class of level l splits into
+                // its zeros and its ones (ones counted over the class's range)
+                for (uint32_t q0 = 0; q0 < base; q0 += 32) {
+                    const uint32_t q = q0 + lane;
+                    const bool act = q < base;
+                    const uint32_t c = act ? sm.cnt[base + q] : 0u;
+                    const uint32_t s0 = act ? sm.loc[base + q] : 0u;
+                    uint32_t ob[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const uint32_t p = e ? s0 + c : s0;
+                        const uint32_t w = p >> 5, r = p & 31u;
+                        const uint32_t wc = min(w, (uint32_t)kBsWords - 1u);
+                        const uint32_t zw = __shfl_sync(kFull, wex, wc >> 6) + sm.zloc[wc];
+                        uint32_t o;
+                        if (w >= (uint32_t)kBsWords) {
+                            o = (uint32_t)kBsTile - zt;
+                        } else {
+                            o = w * 32u - zw;
+                            if (r) o += __popc(sm.lvl[w] & ((1u << r) - 1u));
+                        }
+                        ob[e] = o;
+                    }
+                    if (act) {
+                        const uint32_t ones = ob[1] - ob[0];
+                        sm.cnt[2 * base + 2 * q] = c - ones;
+                        sm.cnt[2 * base + 2 * q + 1] = ones;
+                    }
+                }
+                __syncwarp();
+                if (l + 1 < h) level_tables(l + 1);
+            }
 
             // copy every class's bits to its interval start in level c + l
             {
                 const uint32_t wt = sm.wtot[l];
                 uint64_t *lv = t.bv + (uint64_t)(rt.c + l) * t.W;
                 for (uint32_t k = tid; k < wt; k += kThreads) {
-                    uint32_t lo = 0, hi = base;
+                    uint32_t lo = 0, hi = base;     // last class with wpre <= k
                     while (hi - lo > 1) {
                         const uint32_t mid = (lo + hi) >> 1;
                         if (sm.wpre[base + mid] <= k) lo = mid; else hi = mid;
@@ -914,7 +960,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
                     const uint32_t src = sm.loc[idx] + (uint32_t)(wb + blo - gs);
                     const uint64_t val = extract_bits(sm.lvl, src, bhi - blo) << blo;
-                    if (ge == t.n) bhi = 64;
+                    if (ge == t.n) bhi = 64;       // bits past n belong to the last interval
                     if (blo == 0 && bhi == 64) {
                         lv[word] = val;
                     } else {
@@ -925,36 +971,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 }
             }
 
-            // class counts of level l + 1: each class splits into its zeros and ones
-            for (uint32_t q = tid; q < base; q += kThreads) {
-                const uint32_t c = sm.cnt[base + q];
-                const uint32_t s0 = sm.loc[base + q], s1 = s0 + c;
-                auto ones_before = [&](uint32_t p) {
-                    const uint32_t w = p >> 5, r = p & 31u;
-                    uint32_t o = w * 32u - sm.zoff[w];
-                    if (r) o += __popc(sm.lvl[w] & ((1u << r) - 1u));
-                    return o;
-                };
-                const uint32_t ones = ones_before(s1) - ones_before(s0);
-                sm.cnt[2 * base + 2 * q] = c - ones;
-                sm.cnt[2 * base + 2 * q + 1] = ones;
-            }
-
             // stable split of every later plane by plane l
             if (l + 1 < h) {
-                uint32_t mz[5], mo[5];
-                compress_moves(~mword, mz);
-                compress_moves(mword, mo);
-                const uint32_t nz = 32u - __popc(mword);
-                const uint32_t dz = zo, d1 = zt + tid * 32u - zo;
+                uint32_t mz0[5], mo0[5], mz1[5], mo1[5];
+                compress_moves(~m0, mz0);
+                compress_moves(m0, mo0);
+                compress_moves(~m1, mz1);
+                compress_moves(m1, mo1);
+                const uint32_t dz = zo, d1 = zt + w0 * 32u - zo;
+                const uint32_t nz = z0 + z1, no = 64u - nz;
                 for (uint32_t k = l + 1; k < h; ++k) {
-                    const uint32_t x = cur[k][tid];
-                    place_bits(nxt[k], dz, compress_apply(x, ~mword, mz), nz);
-                    place_bits(nxt[k], d1, compress_apply(x, mword, mo), 32u - nz);
-                    cur[k][tid] = 0;
+                    const uint32_t x0 = cur[k][w0], x1 = cur[k][w0 + 1];
+                    const uint64_t pz = (uint64_t)compress_apply(x0, ~m0, mz0) |
+                                        ((uint64_t)compress_apply(x1, ~m1, mz1) << z0);
+                    const uint64_t po = (uint64_t)compress_apply(x0, m0, mo0) |
+                                        ((uint64_t)compress_apply(x1, m1, mo1) << (32u - z0));
+                    place_bits(nxt[k], dz, pz, nz);
+                    place_bits(nxt[k], d1, po, no);
+                    cur[k][w0] = 0;
+                    cur[k][w0 + 1] = 0;
                 }
                 if (tid == 0)
-                    for (uint32_t k = l + 1; k < h; ++k) cur[k][kBsWords] = 0;
+                    for (uint32_t k = l + 1; k < h; ++k) cur[k][kBsWords] = cur[k][kBsWords + 1] = 0;
             }
             __syncthreads();
         }
