@@ -323,6 +323,148 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched workload: one graph replay per kind vs one wt_build / wm_build per text
+
+def run_batched(args):
+    import torch
+    import paper_1702_07578_gb300 as wtg
+    import synth
+
+    rank, local, world, pg = dist()
+    torch.cuda.set_device(local)
+    count = args.batch_count
+    specs = synth.batch_specs(count)
+    texts_h = synth.batch_texts(specs)
+    sigmas = [s for _, s, _ in specs]
+    total = sum(t.size for t in texts_h)
+    texts = [torch.from_numpy(t.view(np.int16)).cuda() for t in texts_h]
+    stream = torch.cuda.Stream()
+
+    def outputs():
+        bv = [torch.empty((wtg.wt_levels(sg), wtg.wt_words_per_level(t.numel())), dtype=torch.int64,
+                          device="cuda") for t, sg in zip(texts, sigmas)]
+        zz = [torch.empty((max(wtg.wt_levels(sg), 1),), dtype=torch.int64, device="cuda") for sg in sigmas]
+        return bv, zz
+
+    res = {}
+    tune = os.path.join(tempfile.gettempdir(), f"wt_tune_{os.getpid()}.json")
+    os.environ.setdefault("WT_TUNE_CACHE", tune)
+    plans = {}
+    for kind in (wtg.WT_TREE, wtg.WT_MATRIX):
+        bv, zz = outputs()
+        best = wtg.wt_autotune_batched(kind, texts, sigmas, bv, zz if kind else None, stream=stream)
+        plans[kind] = (wtg.WtBatchPlan(kind, texts, sigmas, bv, zz if kind else None, stream=stream), best)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            for kind in plans:
+                plans[kind][0].launch()
+        stream.synchronize()
+        barrier(pg)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for kind in plans:
+                plans[kind][0].launch()
+        e1.record(stream)
+        stream.synchronize()
+    ms = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
+    value = world * 2 * total / (ms / 1e3)
+
+    # the same texts, one plain build per text (per-text workspace, resident inputs)
+    ws = [torch.empty((max(wtg.wt_workspace_size(wtg.WT_TREE, 2, t.numel(), sg),
+                           wtg.wt_workspace_size(wtg.WT_MATRIX, 2, t.numel(), sg)),),
+                      dtype=torch.uint8, device="cuda") for t, sg in zip(texts, sigmas)]
+    bvp, zzp = outputs()
+
+    def plain_step():
+        for i, (t, sg) in enumerate(zip(texts, sigmas)):
+            wtg.wt_build(t, sg, bv=bvp[i], ws=ws[i], stream=stream)
+            wtg.wm_build(t, sg, bv=bvp[i], zeros=zzp[i], ws=ws[i], stream=stream)
+
+    with torch.cuda.stream(stream):
+        plain_step()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        plain_step()
+        e1.record(stream)
+        stream.synchronize()
+        plain_wall = time.perf_counter() - t0
+    plain_ms = max(e0.elapsed_time(e1), plain_wall * 1e3)
+    plain_value = world * 2 * total / (plain_ms / 1e3)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "input symbols/s, batched WT+WM construction (4096 texts) vs per-text launches",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16", "data": "synthetic",
+        "config": {"workload": f"{count} texts, length floor(2^(10+10u)), sigma in {{2^4,2^8,2^12,2^16}}, "
+                               f"uint16, Zipf(0.8) over per-text permutations",
+                   "symbols": total, "builds_per_step": 2 * count,
+                   "symbols_per_block": {"wt": plans[0][1], "wm": plans[1][1]},
+                   "launch": "one CUDA graph replay per kind per step"},
+        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
+                  "launch": f"{2 * count} wt_build/wm_build calls per step"},
+        "speedup_vs_plain": value / plain_value,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# served workload: Poisson arrivals into the serving loop
+
+def run_served(args):
+    import torch
+    import paper_1702_07578_gb300 as wtg
+    import synth
+
+    rank, local, world, pg = dist()
+    torch.cuda.set_device(local)
+    reqs = synth.request_specs(args.requests, args.rate, max_log=args.served_max_log)
+    pool = {}
+    for i, (_, n, sg, zipf, kind, ts) in enumerate(reqs[: args.pool]):
+        pool[i] = synth.request_text(n, sg, zipf, ts)
+    srv = wtg.WtServer(hbm_budget_bytes=64 << 30, max_batch=32, streams=4, device=local)
+    tickets = []
+    t0 = time.perf_counter()
+    sym = 0
+    for i, (ta, n, sg, zipf, kind, ts) in enumerate(reqs):
+        T = pool[i % args.pool]
+        sgm = reqs[i % args.pool][2]
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+        tickets.append(srv.submit(k, T, sgm))
+        sym += T.size
+    for tk in tickets:
+        srv.wait(tk)
+        srv.release(tk)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "served WT/WM construction: symbols/s and latency under Poisson arrivals",
+        "value": sym / wall, "unit": UNIT, "n_gpus": world, "steps": args.requests, "warmup": 0,
+        "ms_per_step": wall * 1e3 / max(args.requests, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
+        "config": {"workload": f"Poisson arrivals at {args.rate} req/s, length log-uniform "
+                               f"[2^12, 2^{args.served_max_log}], sigma in {{2^8, 2^16}}, uniform or Zipf(1.0), "
+                               f"WT or WM; {args.pool} distinct texts reused", "hbm_budget": "64 GB",
+                   "requests": args.requests, "max_batch": 32, "streams": 4},
+        "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"]},
+        "completed": st["completed"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,7 +472,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bytes",
-                    choices=["bytes", "small", "large_alphabet"])
+                    choices=["bytes", "small", "large_alphabet", "batched", "served"])
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=400.0, help="served: arrivals per second")
+    ap.add_argument("--pool", type=int, default=128, help="served: distinct texts")
+    ap.add_argument("--served-max-log", type=int, default=26)
     ap.add_argument("--n-log2", type=int, default=None,
                     help="text length 2^k (smaller cases for profiler captures)")
     ap.add_argument("--oracle-sample-log2", type=int, default=26)
@@ -340,6 +487,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args)
 
 

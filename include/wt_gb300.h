@@ -142,6 +142,42 @@ wt_status wt_batched_workspace_size(wt_kind kind, wt_symtype type, const wt_text
 wt_status wt_build_batched(wt_kind kind, wt_symtype type, const wt_text_desc *h_descs,
                            uint32_t count, void *d_ws, size_t ws_bytes, void *stream);
 
+/* ---- batched construction replayed from a CUDA graph ------------------------
+ * For a batch whose shapes repeat (same count, same n and sigma per text):
+ * wt_batch_plan_create plans the build, uploads the descriptors into the
+ * workspace and records every kernel of the build once into a CUDA graph by
+ * stream capture on `stream` (which must not be the legacy default stream;
+ * nothing executes during the capture).  wt_batch_plan_launch replays the
+ * graph: one launch for the whole batch.  wt_batch_plan_update replaces the
+ * device pointers of the texts and outputs (same n and sigma per text, else
+ * WT_ERR_INVALID_ARG): it waits for the stream, then copies the new
+ * descriptors into the workspace on the stream, in place, so the same graph
+ * builds the new texts.  The workspace (size from wt_batched_workspace_size)
+ * and every buffer named by the descriptors must stay valid while the plan is
+ * used.  symbols_per_block: symbols one build block processes, a multiple of
+ * 32768 up to 2^24; 0 takes the value the autotuner stored for batches of this
+ * shape (WT_TUNE_CACHE), else the default.  The plan holds host memory and the
+ * graph; wt_batch_plan_destroy frees them. */
+typedef struct wt_batch_plan wt_batch_plan;
+
+wt_status wt_batch_plan_create(wt_kind kind, wt_symtype type, const wt_text_desc *h_descs, uint32_t count,
+                               uint32_t symbols_per_block, void *d_ws, size_t ws_bytes, void *stream,
+                               wt_batch_plan **out);
+wt_status wt_batch_plan_update(wt_batch_plan *plan, const wt_text_desc *h_descs, void *stream);
+wt_status wt_batch_plan_launch(wt_batch_plan *plan, void *stream);
+uint32_t wt_batch_plan_symbols_per_block(const wt_batch_plan *plan);
+void wt_batch_plan_destroy(wt_batch_plan *plan);
+
+/* Autotuner: builds the batch (for real, into its output buffers) with each
+ * candidate symbols-per-block value (32768, 65536, 131072, 262144), times three
+ * builds of each with CUDA events on `stream`, and returns the fastest.  If the
+ * environment variable WT_TUNE_CACHE names a file, the choice is stored there
+ * (a JSON object) under a key made of the kind, the storage width and buckets
+ * of the batch's count, total and largest length and rounds; plans created with
+ * symbols_per_block = 0 look it up.  Synchronises the stream. */
+wt_status wt_autotune_batched(wt_kind kind, wt_symtype type, const wt_text_desc *h_descs, uint32_t count,
+                              void *d_ws, size_t ws_bytes, void *stream, uint32_t *best_symbols_per_block);
+
 /* ---- serving -------------------------------------------------------------
  * A server owns device memory (bounded by hbm_budget_bytes) and a set of
  * CUDA streams on one device.  Requests (host texts) are admitted while

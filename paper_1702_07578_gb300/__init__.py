@@ -243,3 +243,67 @@ class WtServer:
             self.close()
         except Exception:
             pass
+
+
+class WtBatchPlan:
+    """wt_batch_plan_*: a batched build recorded once into a CUDA graph, then replayed.
+
+    ``stream`` must be a non-default torch.cuda.Stream (graph capture).  The texts,
+    outputs and workspace must stay alive while the plan is used.
+    """
+
+    def __init__(self, kind, texts, sigmas, bvs, zeros=None, ws=None, stream=None,
+                 symbols_per_block=0):
+        torch = _torch()
+        self.kind = kind
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        st = _symtype(texts[0]) if texts else WT_U8
+        if ws is None:
+            sz = wt_batched_workspace_size(kind, st, [t.numel() for t in texts], sigmas)
+            ws = torch.empty((max(sz, 1),), dtype=torch.uint8, device="cuda")
+        self.ws = ws
+        self._refs = (texts, bvs, zeros)
+        arr = _descs(texts, sigmas, bvs, zeros if kind == WT_MATRIX else None)
+        h = ctypes.c_void_p()
+        _check(lib().wt_batch_plan_create(kind, st, arr, len(texts), int(symbols_per_block),
+                                          _ptr(ws), ws.numel(), _stream(self.stream),
+                                          ctypes.byref(h)), "wt_batch_plan_create")
+        self._h = h
+        self._sigmas = list(sigmas)
+
+    @property
+    def symbols_per_block(self):
+        return int(lib().wt_batch_plan_symbols_per_block(self._h))
+
+    def update(self, texts, bvs, zeros=None):
+        self._refs = (texts, bvs, zeros)
+        arr = _descs(texts, self._sigmas, bvs, zeros if self.kind == WT_MATRIX else None)
+        _check(lib().wt_batch_plan_update(self._h, arr, _stream(self.stream)), "wt_batch_plan_update")
+
+    def launch(self):
+        _check(lib().wt_batch_plan_launch(self._h, _stream(self.stream)), "wt_batch_plan_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wt_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wt_autotune_batched(kind, texts, sigmas, bvs, zeros=None, ws=None, stream=None):
+    """Times the candidate symbols-per-block values on this batch; returns the best."""
+    torch = _torch()
+    st = _symtype(texts[0])
+    if ws is None:
+        sz = wt_batched_workspace_size(kind, st, [t.numel() for t in texts], sigmas)
+        ws = torch.empty((max(sz, 1),), dtype=torch.uint8, device="cuda")
+    arr = _descs(texts, sigmas, bvs, zeros if kind == WT_MATRIX else None)
+    best = ctypes.c_uint32(0)
+    _check(lib().wt_autotune_batched(kind, st, arr, len(texts), _ptr(ws), ws.numel(), _stream(stream),
+                                     ctypes.byref(best)), "wt_autotune_batched")
+    return best.value

@@ -144,6 +144,16 @@ SIGNATURES = {
     "wt_server_destroy": (None, [_C.c_void_p]),
     "wt_build_static_ws": (_C.c_int, [_C.c_void_p, _C.c_int, _C.c_uint64, _C.c_uint64,
                                       _C.c_void_p, _C.c_void_p]),
+    "wt_batch_plan_create": (_C.c_int, [_C.c_int, _C.c_int, _C.POINTER(WtTextDesc), _C.c_uint32,
+                                        _C.c_uint32, _C.c_void_p, _C.c_size_t, _C.c_void_p,
+                                        _C.POINTER(_C.c_void_p)]),
+    "wt_batch_plan_update": (_C.c_int, [_C.c_void_p, _C.POINTER(WtTextDesc), _C.c_void_p]),
+    "wt_batch_plan_launch": (_C.c_int, [_C.c_void_p, _C.c_void_p]),
+    "wt_batch_plan_symbols_per_block": (_C.c_uint32, [_C.c_void_p]),
+    "wt_batch_plan_destroy": (None, [_C.c_void_p]),
+    "wt_autotune_batched": (_C.c_int, [_C.c_int, _C.c_int, _C.POINTER(WtTextDesc), _C.c_uint32,
+                                       _C.c_void_p, _C.c_size_t, _C.c_void_p,
+                                       _C.POINTER(_C.c_uint32)]),
     "wt_profile_enable": (None, [_C.c_int]),
     "wt_profile_read": (_C.c_int, [_C.POINTER(WtProfile), _C.c_int]),
 }

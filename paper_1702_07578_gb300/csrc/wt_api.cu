@@ -23,6 +23,7 @@ struct Plan {
     uint32_t groups_ub[kMaxRounds] = {};
     uint32_t blocks_ub[kMaxRounds] = {};
     uint32_t width[kMaxRounds] = {};
+    uint32_t gelems[kMaxRounds] = {};     // symbols per build block in each round
     size_t off_ctl = 0, off_texts = 0, off_jobs[2] = {}, off_jobhist[2] = {};
     size_t off_ghist = 0, off_gexcl = 0, off_btail = 0, off_bflag = 0, off_bcarry = 0;
     std::vector<size_t> off_buf[2];
@@ -39,11 +40,19 @@ uint32_t levels_of(uint64_t sigma)
     return L;
 }
 
+// Smallest symbols-per-block choice; workspace sizes are computed with it, so any
+// choice (a multiple of it) fits in a workspace of the reported size.
+constexpr uint32_t kMinSpb = 32768;
+
+bool valid_spb(uint32_t spb) { return spb == 0 || (spb % kMinSpb == 0 && spb <= (1u << 24)); }
+
 // Checks the texts and lays out the workspace.  With check_ptrs == false only
-// sizes are validated (workspace queries).
+// sizes are validated (workspace queries).  spb: symbols per build block
+// (0 = the default for the round's symbol width).
 wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t count, bool check_ptrs,
-                    Plan &p)
+                    Plan &p, uint32_t spb = 0)
 {
+    if (!valid_spb(spb)) return WT_ERR_INVALID_ARG;
     if (kind != WT_TREE && kind != WT_MATRIX) return WT_ERR_INVALID_ARG;
     if (type != WT_U8 && type != WT_U16 && type != WT_U32) return WT_ERR_INVALID_ARG;
     if (count > 0 && t == nullptr) return WT_ERR_INVALID_ARG;
@@ -93,7 +102,8 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
     for (uint32_t r = 0; r < p.rounds; ++r) {
         if (slot_acc[r] >= (1ull << 31)) return WT_ERR_INVALID_ARG;
         p.width[r] = width[r] ? width[r] : 1;
-        const uint64_t ge = (uint64_t)group_elems(p.width[r]);
+        p.gelems[r] = spb ? spb : (uint32_t)group_elems(p.width[r]);
+        const uint64_t ge = p.gelems[r];
         for (uint32_t i = 0; i < count; ++i) {
             const TextInfo &ti = p.texts[i];
             const uint32_t ns = ti.nslots[r];
@@ -149,9 +159,9 @@ wt_status ensure_configured()
     return WT_OK;
 }
 
-wt_status run_plan(wt_kind kind, Plan &p, void *d_ws, size_t ws_bytes, cudaStream_t s)
+// Points the re-sorted text buffers of the plan into the workspace.
+wt_status prepare(Plan &p, void *d_ws, size_t ws_bytes)
 {
-    if (p.count == 0) return WT_OK;
     if (d_ws == nullptr || ws_bytes < p.bytes) return WT_ERR_OUT_OF_MEMORY;
     if (reinterpret_cast<uintptr_t>(d_ws) % 256) return WT_ERR_INVALID_ARG;
     wt_status st = ensure_configured();
@@ -162,12 +172,27 @@ wt_status run_plan(wt_kind kind, Plan &p, void *d_ws, size_t ws_bytes, cudaStrea
         ti.buf[0] = ti.L > kChunk ? ws + p.off_buf[0][i] : nullptr;
         ti.buf[1] = ti.L > 2 * kChunk ? ws + p.off_buf[1][i] : nullptr;
     }
+    return WT_OK;
+}
+
+// Copies the text descriptors into the workspace (from `src`, host memory).
+wt_status upload(const Plan &p, const TextInfo *src, void *d_ws, cudaStream_t s)
+{
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    TextInfo *dtexts = reinterpret_cast<TextInfo *>(ws + p.off_texts);
+    if (cudaMemcpyAsync(dtexts, src, sizeof(TextInfo) * p.count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return WT_ERR_CUDA;
+    return WT_OK;
+}
+
+// Every kernel of the build, in stream order; reads the descriptors from the
+// workspace.  Nothing here touches host memory, so it can be captured in a graph.
+wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
+{
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + p.off_ctl);
     TextInfo *dtexts = reinterpret_cast<TextInfo *>(ws + p.off_texts);
     if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) return WT_ERR_CUDA;
-    if (cudaMemcpyAsync(dtexts, p.texts.data(), sizeof(TextInfo) * p.count, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-        return WT_ERR_CUDA;
     if (kind == WT_MATRIX && launch_zero_z(dtexts, p.count, s) != cudaSuccess) return WT_ERR_CUDA;
     for (uint32_t r = 0; r < p.rounds; ++r) {
         RoundArgs a{};
@@ -187,7 +212,7 @@ wt_status run_plan(wt_kind kind, Plan &p, void *d_ws, size_t ws_bytes, cudaStrea
         a.pnslots = r ? p.nslots[r - 1] : 0;
         a.round = r;
         a.kind = (uint32_t)kind;
-        a.gelems = (uint32_t)group_elems(p.width[r]);
+        a.gelems = p.gelems[r];
         a.groups_ub = p.groups_ub[r];
         a.blocks_ub = p.blocks_ub[r];
         for (uint32_t i = 0; i < p.count; ++i) {
@@ -198,6 +223,15 @@ wt_status run_plan(wt_kind kind, Plan &p, void *d_ws, size_t ws_bytes, cudaStrea
         if (launch_round(a, p.width[r], s) != cudaSuccess) return WT_ERR_CUDA;
     }
     return WT_OK;
+}
+
+wt_status run_plan(wt_kind kind, Plan &p, void *d_ws, size_t ws_bytes, cudaStream_t s)
+{
+    if (p.count == 0) return WT_OK;
+    wt_status st = prepare(p, d_ws, ws_bytes);
+    if (st == WT_OK) st = upload(p, p.texts.data(), d_ws, s);
+    if (st == WT_OK) st = launch(kind, p, d_ws, s);
+    return st;
 }
 
 wt_status single(wt_kind kind, const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv,
@@ -241,7 +275,7 @@ wt_status wt_workspace_size(wt_kind kind, wt_symtype type, uint64_t n, uint64_t 
     if (bytes == nullptr) return WT_ERR_INVALID_ARG;
     HostText h{nullptr, n, sigma, nullptr, nullptr};
     Plan p;
-    wt_status st = make_plan(kind, type, &h, 1, false, p);
+    wt_status st = make_plan(kind, type, &h, 1, false, p, kMinSpb);
     if (st == WT_OK) *bytes = p.bytes;
     return st;
 }
@@ -278,7 +312,7 @@ wt_status wt_batched_workspace_size(wt_kind kind, wt_symtype type, const wt_text
     for (uint32_t i = 0; i < count; ++i)
         h[i] = HostText{nullptr, h_descs[i].n, h_descs[i].sigma, nullptr, nullptr};
     Plan p;
-    wt_status st = make_plan(kind, type, h.data(), count, false, p);
+    wt_status st = make_plan(kind, type, h.data(), count, false, p, kMinSpb);
     if (st == WT_OK) *bytes = p.bytes;
     return st;
 }
@@ -436,3 +470,261 @@ extern "C" wt_status wt_build_static_ws(const void *d_text, wt_symtype type, uin
     if (st != WT_OK) return st;
     return run_plan(WT_TREE, p, ws, kStaticScratchBytes, static_cast<cudaStream_t>(stream));
 }
+
+// ---------------------------------------------------------------------------
+// Batched build recorded once into a CUDA graph and replayed; autotuner for the
+// symbols per build block with a JSON cache file.
+
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <string>
+
+namespace wtg {
+namespace {
+
+struct BatchPlanImpl {
+    wt_kind kind = WT_TREE;
+    wt_symtype type = WT_U8;
+    Plan plan;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    TextInfo *h_desc = nullptr;        // pinned copy of the descriptors (upload source)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> n, sigma;
+    uint32_t spb = 0;
+};
+
+const uint32_t kSpbCandidates[] = {32768, 65536, 131072, 262144};
+
+uint32_t ilog2(uint64_t x)
+{
+    uint32_t r = 0;
+    while (x > 1) { x >>= 1; ++r; }
+    return r;
+}
+
+// Cache key: kind, storage width, and buckets of the batch's shape.
+std::string tune_key(wt_kind kind, wt_symtype type, const wt_text_desc *d, uint32_t count)
+{
+    uint64_t total = 0, maxn = 0;
+    uint32_t maxL = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        total += d[i].n;
+        maxn = d[i].n > maxn ? d[i].n : maxn;
+        uint32_t L = levels_of(d[i].sigma);
+        maxL = L > maxL ? L : maxL;
+    }
+    char buf[128];
+    snprintf(buf, sizeof(buf), "k%d_w%d_c%u_t%u_m%u_L%u", (int)kind, (int)type, ilog2(count + 1), ilog2(total + 1),
+             ilog2(maxn + 1), (maxL + 7) / 8);
+    return buf;
+}
+
+std::mutex g_tune_mu;
+
+std::map<std::string, uint32_t> read_cache(const char *path)
+{
+    std::map<std::string, uint32_t> m;
+    FILE *f = path ? fopen(path, "r") : nullptr;
+    if (!f) return m;
+    std::string s;
+    char chunk[4096];
+    size_t k;
+    while ((k = fread(chunk, 1, sizeof(chunk), f)) > 0) s.append(chunk, k);
+    fclose(f);
+    size_t pos = 0;
+    while ((pos = s.find('"', pos)) != std::string::npos) {      // "key": value pairs
+        size_t end = s.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        std::string key = s.substr(pos + 1, end - pos - 1);
+        size_t colon = s.find(':', end);
+        if (colon == std::string::npos) break;
+        m[key] = (uint32_t)strtoul(s.c_str() + colon + 1, nullptr, 10);
+        pos = colon + 1;
+    }
+    return m;
+}
+
+void write_cache(const char *path, const std::map<std::string, uint32_t> &m)
+{
+    if (!path) return;
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{");
+    bool first = true;
+    for (auto &kv : m) {
+        fprintf(f, "%s\n  \"%s\": %u", first ? "" : ",", kv.first.c_str(), kv.second);
+        first = false;
+    }
+    fprintf(f, "\n}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+uint32_t cached_spb(wt_kind kind, wt_symtype type, const wt_text_desc *d, uint32_t count)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto m = read_cache(getenv("WT_TUNE_CACHE"));
+    auto it = m.find(tune_key(kind, type, d, count));
+    return it == m.end() || !valid_spb(it->second) ? 0u : it->second;
+}
+
+wt_status to_host_texts(const wt_text_desc *d, uint32_t count, std::vector<HostText> &h)
+{
+    if (count > 0 && d == nullptr) return WT_ERR_INVALID_ARG;
+    h.resize(count);
+    for (uint32_t i = 0; i < count; ++i) h[i] = HostText{d[i].d_text, d[i].n, d[i].sigma, d[i].d_bv, d[i].d_zeros};
+    return WT_OK;
+}
+
+}  // namespace
+}  // namespace wtg
+
+struct wt_batch_plan {
+    wtg::BatchPlanImpl impl;
+};
+
+extern "C" {
+
+wt_status wt_batch_plan_create(wt_kind kind, wt_symtype type, const wt_text_desc *h_descs, uint32_t count,
+                               uint32_t symbols_per_block, void *d_ws, size_t ws_bytes, void *stream,
+                               wt_batch_plan **out)
+{
+    using namespace wtg;
+    if (out == nullptr || stream == nullptr) return WT_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<HostText> h;
+    wt_status st = to_host_texts(h_descs, count, h);
+    if (st != WT_OK) return st;
+    const uint32_t spb = symbols_per_block ? symbols_per_block : cached_spb(kind, type, h_descs, count);
+    wt_batch_plan *bp = new wt_batch_plan();
+    BatchPlanImpl &b = bp->impl;
+    b.kind = kind;
+    b.type = type;
+    b.ws = d_ws;
+    b.ws_bytes = ws_bytes;
+    b.spb = spb;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = make_plan(kind, type, h.data(), count, true, b.plan, spb);
+    if (st == WT_OK && count > 0) st = prepare(b.plan, d_ws, ws_bytes);
+    if (st == WT_OK && count > 0) {
+        if (cudaMallocHost(reinterpret_cast<void **>(&b.h_desc), sizeof(TextInfo) * count) != cudaSuccess)
+            st = WT_ERR_OUT_OF_MEMORY;
+    }
+    if (st == WT_OK && count > 0) {
+        for (uint32_t i = 0; i < count; ++i) {
+            b.h_desc[i] = b.plan.texts[i];
+            b.n.push_back(h_descs[i].n);
+            b.sigma.push_back(h_descs[i].sigma);
+        }
+        st = upload(b.plan, b.h_desc, d_ws, s);
+    }
+    if (st == WT_OK && count > 0) {
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = WT_ERR_CUDA;
+        } else {
+            wt_status ls = launch(kind, b.plan, d_ws, s);
+            cudaError_t e = cudaStreamEndCapture(s, &b.graph);
+            if (ls != WT_OK) st = ls;
+            else if (e != cudaSuccess) st = WT_ERR_CUDA;
+            else if (cudaGraphInstantiate(&b.exec, b.graph, 0) != cudaSuccess) st = WT_ERR_CUDA;
+        }
+    }
+    if (st != WT_OK) {
+        wt_batch_plan_destroy(bp);
+        return st;
+    }
+    *out = bp;
+    return WT_OK;
+}
+
+wt_status wt_batch_plan_update(wt_batch_plan *bp, const wt_text_desc *h_descs, void *stream)
+{
+    using namespace wtg;
+    if (bp == nullptr || stream == nullptr) return WT_ERR_INVALID_ARG;
+    BatchPlanImpl &b = bp->impl;
+    const uint32_t count = b.plan.count;
+    if (count == 0) return WT_OK;
+    if (h_descs == nullptr) return WT_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (h_descs[i].n != b.n[i] || h_descs[i].sigma != b.sigma[i]) return WT_ERR_INVALID_ARG;
+        const uint32_t L = b.plan.texts[i].L;
+        if (L > 0 && h_descs[i].n > 0 && (h_descs[i].d_text == nullptr || h_descs[i].d_bv == nullptr))
+            return WT_ERR_INVALID_ARG;
+        if (b.kind == WT_MATRIX && L > 0 && h_descs[i].d_zeros == nullptr) return WT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return WT_ERR_CUDA;   // the pinned copy may still be read
+    for (uint32_t i = 0; i < count; ++i) {
+        b.h_desc[i].text = h_descs[i].d_text;
+        b.h_desc[i].bv = h_descs[i].d_bv;
+        b.h_desc[i].zeros = b.kind == WT_MATRIX ? h_descs[i].d_zeros : nullptr;
+    }
+    return upload(b.plan, b.h_desc, b.ws, s);
+}
+
+wt_status wt_batch_plan_launch(wt_batch_plan *bp, void *stream)
+{
+    if (bp == nullptr) return WT_ERR_INVALID_ARG;
+    if (bp->impl.exec == nullptr) return WT_OK;                       // empty batch
+    if (cudaGraphLaunch(bp->impl.exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return WT_ERR_CUDA;
+    return WT_OK;
+}
+
+uint32_t wt_batch_plan_symbols_per_block(const wt_batch_plan *bp) { return bp ? bp->impl.spb : 0; }
+
+void wt_batch_plan_destroy(wt_batch_plan *bp)
+{
+    if (bp == nullptr) return;
+    if (bp->impl.exec) cudaGraphExecDestroy(bp->impl.exec);
+    if (bp->impl.graph) cudaGraphDestroy(bp->impl.graph);
+    if (bp->impl.h_desc) cudaFreeHost(bp->impl.h_desc);
+    delete bp;
+}
+
+wt_status wt_autotune_batched(wt_kind kind, wt_symtype type, const wt_text_desc *h_descs, uint32_t count, void *d_ws,
+                              size_t ws_bytes, void *stream, uint32_t *best_symbols_per_block)
+{
+    using namespace wtg;
+    if (best_symbols_per_block == nullptr) return WT_ERR_INVALID_ARG;
+    std::vector<HostText> h;
+    wt_status st = to_host_texts(h_descs, count, h);
+    if (st != WT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return WT_ERR_CUDA;
+    float best_ms = 0.f;
+    uint32_t best = 0;
+    for (uint32_t spb : kSpbCandidates) {
+        Plan p;
+        st = make_plan(kind, type, h.data(), count, true, p, spb);
+        if (st != WT_OK) break;
+        st = run_plan(kind, p, d_ws, ws_bytes, s);                      // warm-up
+        if (st != WT_OK) break;
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3 && st == WT_OK; ++rep) st = run_plan(kind, p, d_ws, ws_bytes, s);
+        cudaEventRecord(e1, s);
+        if (st != WT_OK || cudaEventSynchronize(e1) != cudaSuccess) { st = st == WT_OK ? WT_ERR_CUDA : st; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best == 0 || ms < best_ms) { best_ms = ms; best = spb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != WT_OK) return st;
+    *best_symbols_per_block = best;
+    const char *path = getenv("WT_TUNE_CACHE");
+    if (path) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto m = read_cache(path);
+        m[tune_key(kind, type, h_descs, count)] = best;
+        write_cache(path, m);
+    }
+    return WT_OK;
+}
+
+}  // extern "C"

@@ -1029,7 +1029,9 @@ cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s
 cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s)
 {
     if (a.nslots == 0) return cudaSuccess;
-    const bool prof = profile_on();
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    const bool prof = profile_on() && cap == cudaStreamCaptureStatusNone;
     const bool root = a.round == 0 || a.kind == WT_MATRIX;
     if (prof) profile_mark(3, true, s);
     if (root) k_root_jobs<<<(a.ntexts + 255) / 256, 256, 0, s>>>(a);

@@ -86,3 +86,50 @@ def test_batched_symbol_range_error():
     with pytest.raises(wtg.WtError) as e:
         wtg.wt_sync_status(ws)
     assert e.value.code == 2
+
+
+@pytest.mark.parametrize("kind", ["wt", "wm"])
+def test_graph_plan_replay_and_update(kind, tmp_path, monkeypatch):
+    """One graph replay builds the whole batch; after an in-place descriptor update
+    the same graph builds other texts of the same shapes; the autotuner's choice is
+    cached and picked up by a new plan."""
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    monkeypatch.setenv("WT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    specs = synth.batch_specs(64, max_log=16)
+    sigmas = [s for _, s, _ in specs]
+    k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+    A = synth.batch_texts(specs)
+    B = [synth.zipf_text(n, sg, 1.0, ts + 99, np.uint16) for n, sg, ts in specs]
+    ta = [torch_text(t) for t in A]
+    tb = [torch_text(t) for t in B]
+
+    def outs():
+        bv = [torch.empty((wtg.wt_levels(s), wtg.wt_words_per_level(t.numel())), dtype=torch.int64,
+                          device="cuda") for t, s in zip(ta, sigmas)]
+        zz = [torch.empty((max(wtg.wt_levels(s), 1),), dtype=torch.int64, device="cuda")
+              for s in sigmas] if kind == "wm" else None
+        return bv, zz
+
+    bva, za = outs()
+    bvb, zb = outs()
+    stream = torch.cuda.Stream()
+    best = wtg.wt_autotune_batched(k, ta, sigmas, bva, za, stream=stream)
+    assert best in (32768, 65536, 131072, 262144)
+    plan = wtg.WtBatchPlan(k, ta, sigmas, bva, za, stream=stream)
+    assert plan.symbols_per_block == best
+    for _ in range(2):
+        plan.launch()
+    plan.update(tb, bvb, zb)
+    plan.launch()
+    stream.synchronize()
+    for i in range(0, len(A), 5):
+        for T, bv, zz in ((A[i], bva, za), (B[i], bvb, zb)):
+            if kind == "wt":
+                assert np.array_equal(to_u64(bv[i]), oracle.wt(T, sigmas[i])), i
+            else:
+                e, ez = oracle.wm(T, sigmas[i])
+                assert np.array_equal(to_u64(bv[i]), e), i
+                assert np.array_equal(zz[i][:e.shape[0]].cpu().numpy().astype(np.uint64), ez)
+    plan.close()
