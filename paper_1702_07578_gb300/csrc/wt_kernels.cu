@@ -248,36 +248,71 @@ __global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
 // ---------------------------------------------------------------------------
 // a1: class histogram of every group (the first counting-sort phase)
 
-__global__ void __launch_bounds__(kThreads) k_hist(RoundArgs a)
+// Two sub-histograms per warp (even and odd lanes), 257 words apart so that
+// equal classes of the two copies fall in different banks: with skewed texts
+// (Zipf) many lanes of a warp count the same class at once.
+constexpr int kHistThreads = 512;
+constexpr int kHistWarps = kHistThreads / 32;
+constexpr int kHistCopies = 2;
+constexpr int kHistStride = kCols + 1;
+constexpr size_t kHistSmem = sizeof(uint32_t) * kHistWarps * kHistCopies * kHistStride;
+
+__global__ void __launch_bounds__(kHistThreads) k_hist(RoundArgs a)
 {
-    __shared__ uint32_t wh[kWarps][kCols];
+    extern __shared__ __align__(16) uint32_t wh[];
     const uint32_t g = blockIdx.x;
     if (g >= a.ctl->total_groups[a.round]) return;
     const uint32_t slot = find_slot(a.jobs, a.nslots, g);
     const Job jb = a.jobs[slot];
     const TextInfo &t = a.texts[jb.text];
     const RoundText rt = round_text(t, a.round);
-    for (uint32_t i = threadIdx.x; i < kWarps * kCols; i += kThreads) (&wh[0][0])[i] = 0;
+    for (uint32_t i = threadIdx.x; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) wh[i] = 0;
     __syncthreads();
     const uint64_t i0 = (uint64_t)(g - jb.g0) * a.gelems;
     const uint64_t i1 = min((uint64_t)jb.n, i0 + a.gelems);
     const uint32_t shift = rt.rb - rt.h, mask = (1u << rt.h) - 1u;
     const bool check = a.round == 0 && t.sigma < (1ull << t.L);
     const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
-    uint32_t *mine = wh[threadIdx.x >> 5];
+    uint32_t *mine = wh + ((threadIdx.x >> 5) * kHistCopies + (threadIdx.x & (kHistCopies - 1))) * kHistStride;
     bool bad = false;
     const uint8_t *base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
-    for_range(base, rt.in_w, i0, i1, [&](uint32_t, uint32_t v) {
-        bad |= check && v >= sig;
-        bad |= a.round == 0 && t.L < 32 && (v >> t.L) != 0;
-        atomicAdd(&mine[(v >> shift) & mask], 1u);
-    });
+    const uint8_t *lo = base + i0, *hi = base + i1;
+    if (rt.in_w == 1 && (reinterpret_cast<uintptr_t>(lo) & 15u) == 0) {
+        // bytes: whole 16-byte chunks, range checks on whole words
+        const uint32_t top = a.round == 0 && t.L < 8 ? (0xffu << t.L) & 0xffu : 0u;
+        const uint32_t top4 = top * 0x01010101u;
+        const uint4 *v = reinterpret_cast<const uint4 *>(lo);
+        const uint64_t nchunks = (uint64_t)(hi - lo) >> 4;
+        for (uint64_t k = threadIdx.x; k < nchunks; k += kHistThreads) {
+            const uint4 q = __ldg(v + k);
+            const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t x = words[j];
+                bad |= (x & top4) != 0u;
+                if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) atomicAdd(&mine[((x >> (8 * b + shift)) & mask)], 1u);
+            }
+        }
+        for (uint64_t i = i0 + nchunks * 16 + threadIdx.x; i < i1; i += kHistThreads) {
+            const uint32_t x = base[i];
+            bad |= (check && x >= sig) || (x & top) != 0u;
+            atomicAdd(&mine[(x >> shift) & mask], 1u);
+        }
+    } else {
+        for_range(base, rt.in_w, i0, i1, [&](uint32_t, uint32_t v) {
+            bad |= check && v >= sig;
+            bad |= a.round == 0 && t.L < 32 && (v >> t.L) != 0;
+            atomicAdd(&mine[(v >> shift) & mask], 1u);
+        });
+    }
     if (bad) atomicCAS(&a.ctl->status, 0u, (uint32_t)WT_ERR_SYMBOL_RANGE);
     __syncthreads();
-    for (uint32_t col = threadIdx.x; col < kCols; col += kThreads) {
+    for (uint32_t col = threadIdx.x; col < kCols; col += kHistThreads) {
         uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += wh[w][col];
+#pragma unroll 8
+        for (int c = 0; c < kHistWarps * kHistCopies; ++c) s += wh[c * kHistStride + col];
         a.ghist[(size_t)g * kCols + col] = s;
     }
 }
@@ -1007,6 +1042,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 cudaError_t configure_kernels()
 {
     cudaError_t e;
+    e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_build_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_build<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1040,7 +1077,7 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     if (prof) profile_mark(3, false, s);
     if (a.groups_ub == 0) return cudaGetLastError();
     if (prof) profile_mark(1, true, s);
-    k_hist<<<a.groups_ub, kThreads, 0, s>>>(a);
+    k_hist<<<a.groups_ub, kHistThreads, kHistSmem, s>>>(a);
     if (prof) { profile_mark(1, false, s); profile_mark(2, true, s); }
     k_blocksum<<<a.blocks_ub, 256, 0, s>>>(a);
     k_blockscan<<<1, 256, 0, s>>>(a);
