@@ -25,7 +25,7 @@ struct Plan {
     uint32_t width[kMaxRounds] = {};
     uint32_t gelems[kMaxRounds] = {};     // symbols per build block in each round
     size_t off_ctl = 0, off_texts = 0, off_jobs[2] = {}, off_jobhist[2] = {};
-    size_t off_ghist = 0, off_gexcl = 0, off_btail = 0, off_bflag = 0, off_bcarry = 0;
+    size_t off_ghist = 0, off_gexcl = 0, off_thist = 0, off_btail = 0, off_bflag = 0, off_bcarry = 0;
     std::vector<size_t> off_buf[2];
     std::vector<TextInfo> texts;
     size_t bytes = 0;
@@ -60,6 +60,7 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
     p.count = count;
     p.texts.assign(count, TextInfo{});
     uint32_t max_slots = 0, max_groups = 0;
+    uint64_t max_tiles = 0;
     uint64_t slot_acc[kMaxRounds] = {}, group_acc[kMaxRounds] = {};
     uint32_t width[kMaxRounds] = {};
     for (uint32_t i = 0; i < count; ++i) {
@@ -116,6 +117,13 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
         p.blocks_ub[r] = (p.groups_ub[r] + kRowsPerBlock - 1) / kRowsPerBlock;
         if (p.nslots[r] > max_slots) max_slots = p.nslots[r];
         if (p.groups_ub[r] > max_groups) max_groups = p.groups_ub[r];
+        uint64_t tiles = 0;                       // rows of the tile histograms
+        for (uint32_t i = 0; i < count; ++i) {
+            const TextInfo &ti = p.texts[i];
+            const uint32_t ns = ti.nslots[r];
+            if (ns) tiles += ns == 1 ? (ti.n + kTileSyms - 1) / kTileSyms : ti.n / kTileSyms + ns;
+        }
+        if (tiles > max_tiles) max_tiles = tiles;
     }
     const uint32_t max_blocks = (max_groups + kRowsPerBlock - 1) / kRowsPerBlock;
     size_t off = 0;
@@ -130,6 +138,7 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
     for (int k = 0; k < 2; ++k) p.off_jobhist[k] = take(sizeof(uint32_t) * kCols * (size_t)max_slots);
     p.off_ghist = take(sizeof(uint32_t) * kCols * (size_t)max_groups);
     p.off_gexcl = take(sizeof(uint32_t) * kCols * (size_t)max_groups);
+    p.off_thist = take(sizeof(uint32_t) * kCols * (size_t)max_tiles);
     p.off_btail = take(sizeof(uint32_t) * kCols * (size_t)max_blocks);
     p.off_bcarry = take(sizeof(uint32_t) * kCols * (size_t)max_blocks);
     p.off_bflag = take(sizeof(uint32_t) * (size_t)max_blocks);
@@ -204,6 +213,7 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
         a.pjobhist = reinterpret_cast<const uint32_t *>(ws + p.off_jobhist[(r + 1) & 1]);
         a.ghist = reinterpret_cast<uint32_t *>(ws + p.off_ghist);
         a.gexcl = reinterpret_cast<uint32_t *>(ws + p.off_gexcl);
+        a.thist = reinterpret_cast<uint32_t *>(ws + p.off_thist);
         a.btail = reinterpret_cast<uint32_t *>(ws + p.off_btail);
         a.bflag = reinterpret_cast<uint32_t *>(ws + p.off_bflag);
         a.bcarry = reinterpret_cast<uint32_t *>(ws + p.off_bcarry);

@@ -26,6 +26,7 @@ constexpr int kTilesPerGroup = 4;     // tiles one build block processes
 constexpr int kRowsPerBlock = 64;     // groups per block of the segmented scan
 constexpr int kCols = 256;            // histogram columns (2^8 classes per round)
 constexpr int kMaxTreeSigmaLog = 24;  // WT alphabets up to 2^24
+constexpr int kTileSyms = 32768;      // symbols per tile of the bit-sliced build; groups are multiples
 
 // Elements per thread and tile size, by the width of an element in shared memory.
 __host__ __device__ constexpr int elems_per_thread(int width) { return width == 1 ? 32 : 16; }
@@ -55,7 +56,7 @@ struct Job {
     uint32_t text;
     uint32_t g0;             // first group (build block) of this job in the round
     uint32_t ng;             // groups of this job
-    uint32_t pad;
+    uint32_t tile0;          // first row of this job in the tile histograms (kTileSyms symbols per row)
 };
 
 struct Ctl {
@@ -73,6 +74,7 @@ struct RoundArgs {
     const uint32_t *pjobhist;
     uint32_t *ghist;         // [groups][256]: class counts of each group
     uint32_t *gexcl;         // [groups][256]: count of the class in earlier groups of the job
+    uint32_t *thist;         // [tiles][256]: class counts of every kTileSyms symbols of a job
     uint32_t *btail;         // [blocks][256]: segmented-scan block summaries
     uint32_t *bflag;         // [blocks]
     uint32_t *bcarry;        // [blocks][256]

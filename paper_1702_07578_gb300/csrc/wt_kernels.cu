@@ -186,7 +186,7 @@ __global__ void k_root_jobs(RoundArgs a)
     j.text = t;
     j.g0 = 0;
     j.ng = (uint32_t)((x.n + a.gelems - 1) / a.gelems);
-    j.pad = 0;
+    j.tile0 = 0;
     a.jobs[x.slot_base[a.round]] = j;
 }
 
@@ -216,31 +216,40 @@ __global__ void __launch_bounds__(256) k_child_jobs(RoundArgs a)
     j.text = pj.text;
     j.g0 = 0;
     j.ng = (cnt + a.gelems - 1) / a.gelems;
-    j.pad = 0;
+    j.tile0 = 0;
     a.jobs[cb + q] = j;
 }
 
-// Exclusive scan of the group counts over all slots -> g0; total groups.
+// Exclusive scans over all slots of the group counts -> g0 (total groups) and
+// of the tile counts -> tile0.
 __global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
 {
-    __shared__ uint32_t part[1024];
-    uint32_t n = a.nslots;
-    uint32_t per = (n + 1023) / 1024;
-    uint32_t b = threadIdx.x * per, e = min(n, b + per);
-    uint32_t sum = 0;
-    for (uint32_t i = b; i < e; ++i) sum += a.jobs[i].ng;
+    __shared__ uint32_t part[1024], tpart[1024];
+    const uint32_t n = a.nslots;
+    const uint32_t per = (n + 1023) / 1024;
+    const uint32_t b = threadIdx.x * per, e = min(n, b + per);
+    uint32_t sum = 0, tsum = 0;
+    for (uint32_t i = b; i < e; ++i) {
+        sum += a.jobs[i].ng;
+        tsum += (a.jobs[i].n + kTileSyms - 1) / kTileSyms;
+    }
     part[threadIdx.x] = sum;
+    tpart[threadIdx.x] = tsum;
     __syncthreads();
     for (uint32_t d = 1; d < 1024; d <<= 1) {
-        uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
+        const uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
+        const uint32_t tv = threadIdx.x >= d ? tpart[threadIdx.x - d] : 0u;
         __syncthreads();
         part[threadIdx.x] += v;
+        tpart[threadIdx.x] += tv;
         __syncthreads();
     }
-    uint32_t run = part[threadIdx.x] - sum;
+    uint32_t run = part[threadIdx.x] - sum, trun = tpart[threadIdx.x] - tsum;
     for (uint32_t i = b; i < e; ++i) {
         a.jobs[i].g0 = run;
+        a.jobs[i].tile0 = trun;
         run += a.jobs[i].ng;
+        trun += (a.jobs[i].n + kTileSyms - 1) / kTileSyms;
     }
     if (threadIdx.x == 1023) a.ctl->total_groups[a.round] = part[1023];
 }
@@ -266,55 +275,65 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(RoundArgs a)
     const Job jb = a.jobs[slot];
     const TextInfo &t = a.texts[jb.text];
     const RoundText rt = round_text(t, a.round);
-    for (uint32_t i = threadIdx.x; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) wh[i] = 0;
-    __syncthreads();
-    const uint64_t i0 = (uint64_t)(g - jb.g0) * a.gelems;
-    const uint64_t i1 = min((uint64_t)jb.n, i0 + a.gelems);
+    const uint64_t g0 = (uint64_t)(g - jb.g0) * a.gelems;
+    const uint64_t g1 = min((uint64_t)jb.n, g0 + a.gelems);
     const uint32_t shift = rt.rb - rt.h, mask = (1u << rt.h) - 1u;
     const bool check = a.round == 0 && t.sigma < (1ull << t.L);
     const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
     uint32_t *mine = wh + ((threadIdx.x >> 5) * kHistCopies + (threadIdx.x & (kHistCopies - 1))) * kHistStride;
     bool bad = false;
     const uint8_t *base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
-    const uint8_t *lo = base + i0, *hi = base + i1;
-    if (rt.in_w == 1 && (reinterpret_cast<uintptr_t>(lo) & 15u) == 0) {
-        // bytes: whole 16-byte chunks, range checks on whole words
-        const uint32_t top = a.round == 0 && t.L < 8 ? (0xffu << t.L) & 0xffu : 0u;
-        const uint32_t top4 = top * 0x01010101u;
-        const uint4 *v = reinterpret_cast<const uint4 *>(lo);
-        const uint64_t nchunks = (uint64_t)(hi - lo) >> 4;
-        for (uint64_t k = threadIdx.x; k < nchunks; k += kHistThreads) {
-            const uint4 q = __ldg(v + k);
-            const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+    const uint32_t top = a.round == 0 && t.L < 8 ? (0xffu << t.L) & 0xffu : 0u;
+    const uint32_t top4 = top * 0x01010101u;
+    const uint32_t tile_first = jb.tile0 + (uint32_t)(g0 / kTileSyms);
+    uint32_t gsum = 0;                                   // group total of column threadIdx.x
+    // one tile (kTileSyms symbols) at a time: its histogram row, then the group's
+    for (uint64_t i0 = g0, tix = 0; i0 < g1; i0 += kTileSyms, ++tix) {
+        const uint64_t i1 = min(g1, i0 + kTileSyms);
+        for (uint32_t i = threadIdx.x; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) wh[i] = 0;
+        __syncthreads();
+        const uint8_t *lo = base + i0, *hi = base + i1;
+        if (rt.in_w == 1 && (reinterpret_cast<uintptr_t>(lo) & 15u) == 0) {
+            // bytes: whole 16-byte chunks, range checks on whole words
+            const uint4 *v = reinterpret_cast<const uint4 *>(lo);
+            const uint64_t nchunks = (uint64_t)(hi - lo) >> 4;
+            for (uint64_t k = threadIdx.x; k < nchunks; k += kHistThreads) {
+                const uint4 q = __ldg(v + k);
+                const uint32_t words[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t x = words[j];
-                bad |= (x & top4) != 0u;
-                if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t x = words[j];
+                    bad |= (x & top4) != 0u;
+                    if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) atomicAdd(&mine[((x >> (8 * b + shift)) & mask)], 1u);
+                    for (int b = 0; b < 4; ++b) atomicAdd(&mine[((x >> (8 * b + shift)) & mask)], 1u);
+                }
             }
+            for (uint64_t i = i0 + nchunks * 16 + threadIdx.x; i < i1; i += kHistThreads) {
+                const uint32_t x = base[i];
+                bad |= (check && x >= sig) || (x & top) != 0u;
+                atomicAdd(&mine[(x >> shift) & mask], 1u);
+            }
+        } else {
+            for_range(base, rt.in_w, i0, i1, [&](uint32_t, uint32_t v) {
+                bad |= check && v >= sig;
+                bad |= a.round == 0 && t.L < 32 && (v >> t.L) != 0;
+                atomicAdd(&mine[(v >> shift) & mask], 1u);
+            });
         }
-        for (uint64_t i = i0 + nchunks * 16 + threadIdx.x; i < i1; i += kHistThreads) {
-            const uint32_t x = base[i];
-            bad |= (check && x >= sig) || (x & top) != 0u;
-            atomicAdd(&mine[(x >> shift) & mask], 1u);
+        __syncthreads();
+        if (threadIdx.x < (uint32_t)kCols) {
+            const uint32_t col = threadIdx.x;
+            uint32_t s = 0;
+#pragma unroll 8
+            for (int c = 0; c < kHistWarps * kHistCopies; ++c) s += wh[c * kHistStride + col];
+            a.thist[((size_t)tile_first + tix) * kCols + col] = s;
+            gsum += s;
         }
-    } else {
-        for_range(base, rt.in_w, i0, i1, [&](uint32_t, uint32_t v) {
-            bad |= check && v >= sig;
-            bad |= a.round == 0 && t.L < 32 && (v >> t.L) != 0;
-            atomicAdd(&mine[(v >> shift) & mask], 1u);
-        });
+        __syncthreads();
     }
     if (bad) atomicCAS(&a.ctl->status, 0u, (uint32_t)WT_ERR_SYMBOL_RANGE);
-    __syncthreads();
-    for (uint32_t col = threadIdx.x; col < kCols; col += kHistThreads) {
-        uint32_t s = 0;
-#pragma unroll 8
-        for (int c = 0; c < kHistWarps * kHistCopies; ++c) s += wh[c * kHistStride + col];
-        a.ghist[(size_t)g * kCols + col] = s;
-    }
+    if (threadIdx.x < (uint32_t)kCols) a.ghist[(size_t)g * kCols + threadIdx.x] = gsum;
 }
 
 // ---------------------------------------------------------------------------
@@ -674,12 +693,14 @@ namespace {
 
 constexpr int kBsWords = 2 * kThreads;        // words per plane
 constexpr int kBsTile = kBsWords * 32;        // 32768 symbols per tile
+static_assert(kBsTile == kTileSyms, "tile histograms are written per kTileSyms symbols");
 
 struct BsSmem {
     uint32_t plane[2][kChunk][kBsWords + 2];  // current / next planes (+ overflow words)
     uint32_t lvl[kBsWords + 4];               // the current level's plane, tile order
-    uint32_t zloc[kBsWords];                  // zeros before each word inside its warp's range
     uint32_t wsum[kWarps];                    // zeros of each warp's range
+    uint32_t thc[kCols];                      // class counts of the tile (histogram pass)
+    uint32_t tP[kCols + 1];
     uint32_t offq[kCols];                     // class counts of the job before this tile
     uint32_t jP[kCols + 1];
     uint32_t oP[kCols + 1];
@@ -866,40 +887,56 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const uint8_t *in_base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
     const uint32_t w0 = 2u * tid;                    // this thread's words: w0, w0 + 1
 
-    // Class tables of level l (counts already in cnt): tile-order starts
-    // (reversed prefixes), interval starts in the level, destination words.
-    // Run by one warp.
-    auto level_tables = [&](uint32_t l) {
-        const uint32_t base = 1u << l, s = h - l;
-        warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
-                      [&](uint32_t i) { return rev_bits(i, l); },
-                      [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
-        const uint32_t wt = warp_scan_256(
-            base,
-            [&](uint32_t q) {
-                const uint32_t c = sm.cnt[base + q];
-                const uint32_t gs = jb.off + sm.jspos[base + q] + (sm.oP[(q + 1) << s] - sm.oP[q << s]);
-                sm.glo[base + q] = gs;
-                if (c == 0) return 0u;
-                return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
-            },
-            [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
-        if (lane == 0) sm.wtot[l] = wt;
-    };
-
-    for (uint64_t t0 = g_begin; t0 < g_end; t0 += kBsTile) {
+    const uint32_t tile_first = jb.tile0 + (uint32_t)(g_begin / kTileSyms);
+    uint32_t tix = 0;
+    for (uint64_t t0 = g_begin; t0 < g_end; t0 += kBsTile, ++tix) {
         const uint32_t m = (uint32_t)min((uint64_t)kBsTile, g_end - t0);
-        // ---- clear the plane buffers; job offsets before this tile; level-0 tables
-        for (uint32_t i = tid; i < 2 * kChunk * (kBsWords + 2); i += kThreads) (&sm.plane[0][0][0])[i] = 0;
+        // ---- class counts of the tile (from the histogram pass); clear the next-plane buffer
+        for (uint32_t i = tid; i < kChunk * (kBsWords + 2); i += kThreads) (&sm.plane[1][0][0])[i] = 0;
+        if (tid < (uint32_t)kChunk) sm.plane[0][tid][kBsWords] = sm.plane[0][tid][kBsWords + 1] = 0;
+        for (uint32_t q = tid; q < kCols; q += kThreads)
+            sm.thc[q] = a.thist[((size_t)tile_first + tix) * kCols + q];
+        __syncthreads();
         if (warp == 0) {
+            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.thc[i]; }, [](uint32_t i) { return i; },
+                                         [&](uint32_t i, uint32_t v) { sm.tP[i] = v; });
+            if (lane == 0) sm.tP[256] = tot;
+        } else if (warp == 1) {
             uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.offq[i]; }, [](uint32_t i) { return i; },
                                          [&](uint32_t i, uint32_t v) { sm.oP[i] = v; });
             if (lane == 0) sm.oP[256] = tot;
-            if (lane == 0) sm.cnt[1] = m;
-            __syncwarp();
-            level_tables(0);
         }
         __syncthreads();
+        // every level's class counts and interval starts in the level (fold of the
+        // tile counts and of the job offsets; Alg. 1 fold, Sec. 3.1)
+        for (uint32_t idx = tid; idx < kHeap; idx += kThreads) {
+            if (idx == 0) continue;
+            const uint32_t l = 31u - __clz(idx), q = idx - (1u << l);
+            if (l <= h) {
+                const uint32_t s = h - l, lo = q << s, hi = (q + 1) << s;
+                sm.cnt[idx] = sm.tP[hi] - sm.tP[lo];
+                sm.glo[idx] = jb.off + sm.jspos[idx] + (sm.oP[hi] - sm.oP[lo]);
+            }
+        }
+        __syncthreads();
+        // per level (one warp each): class starts in tile order (reversed
+        // prefixes, Obs. 2) and destination words of every class
+        if (warp < h) {
+            const uint32_t l = warp, base = 1u << l;
+            warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
+                          [&](uint32_t i) { return rev_bits(i, l); },
+                          [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
+            const uint32_t wt = warp_scan_256(
+                base,
+                [&](uint32_t q) {
+                    const uint32_t c = sm.cnt[base + q];
+                    if (c == 0) return 0u;
+                    const uint32_t gs = sm.glo[base + q];
+                    return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
+                },
+                [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
+            if (lane == 0) sm.wtot[l] = wt;
+        }
         // ---- load and transpose: plane k holds code bit rb-1-k of every symbol
         {
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
@@ -927,8 +964,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 if (lane >= (uint32_t)d) inc += y;
             }
             const uint32_t zl = inc - z0 - z1;             // zeros before word w0 inside the warp
-            sm.zloc[w0] = zl;
-            sm.zloc[w0 + 1] = zl + z0;
             if (lane == 31) sm.wsum[warp] = inc;
             __syncthreads();
             // zeros before each warp's range; total zeros Z of the tile
@@ -943,39 +978,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             wex -= ws;                                      // lane j: zeros before warp j's words
             const uint32_t zo = __shfl_sync(kFull, wex, warp) + zl;
 
-            if (warp == 0) {
-                // class counts of level l + 1: each class of level l splits into
-                // its zeros and its ones (ones counted over the class's range)
-                for (uint32_t q0 = 0; q0 < base; q0 += 32) {
-                    const uint32_t q = q0 + lane;
-                    const bool act = q < base;
-                    const uint32_t c = act ? sm.cnt[base + q] : 0u;
-                    const uint32_t s0 = act ? sm.loc[base + q] : 0u;
-                    uint32_t ob[2];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const uint32_t p = e ? s0 + c : s0;
-                        const uint32_t w = p >> 5, r = p & 31u;
-                        const uint32_t wc = min(w, (uint32_t)kBsWords - 1u);
-                        const uint32_t zw = __shfl_sync(kFull, wex, wc >> 6) + sm.zloc[wc];
-                        uint32_t o;
-                        if (w >= (uint32_t)kBsWords) {
-                            o = (uint32_t)kBsTile - zt;
-                        } else {
-                            o = w * 32u - zw;
-                            if (r) o += __popc(sm.lvl[w] & ((1u << r) - 1u));
-                        }
-                        ob[e] = o;
-                    }
-                    if (act) {
-                        const uint32_t ones = ob[1] - ob[0];
-                        sm.cnt[2 * base + 2 * q] = c - ones;
-                        sm.cnt[2 * base + 2 * q + 1] = ones;
-                    }
-                }
-                __syncwarp();
-                if (l + 1 < h) level_tables(l + 1);
-            }
 
             // copy every class's bits to its interval start in level c + l
             {
