@@ -286,12 +286,13 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(RoundArgs a)
     const uint32_t top = a.round == 0 && t.L < 8 ? (0xffu << t.L) & 0xffu : 0u;
     const uint32_t top4 = top * 0x01010101u;
     const uint32_t tile_first = jb.tile0 + (uint32_t)(g0 / kTileSyms);
-    uint32_t gsum = 0;                                   // group total of column threadIdx.x
-    // one tile (kTileSyms symbols) at a time: its histogram row, then the group's
+    uint32_t gsum = 0;                                   // running group count of column threadIdx.x
+    for (uint32_t i = threadIdx.x; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) wh[i] = 0;
+    __syncthreads();
+    // one tile (kTileSyms symbols) at a time; a tile's row is the difference of
+    // the running counts after and before it
     for (uint64_t i0 = g0, tix = 0; i0 < g1; i0 += kTileSyms, ++tix) {
         const uint64_t i1 = min(g1, i0 + kTileSyms);
-        for (uint32_t i = threadIdx.x; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) wh[i] = 0;
-        __syncthreads();
         const uint8_t *lo = base + i0, *hi = base + i1;
         if (rt.in_w == 1 && (reinterpret_cast<uintptr_t>(lo) & 15u) == 0) {
             // bytes: whole 16-byte chunks, range checks on whole words
@@ -327,8 +328,8 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(RoundArgs a)
             uint32_t s = 0;
 #pragma unroll 8
             for (int c = 0; c < kHistWarps * kHistCopies; ++c) s += wh[c * kHistStride + col];
-            a.thist[((size_t)tile_first + tix) * kCols + col] = s;
-            gsum += s;
+            a.thist[((size_t)tile_first + tix) * kCols + col] = s - gsum;
+            gsum = s;
         }
         __syncthreads();
     }
@@ -700,6 +701,7 @@ struct BsSmem {
     uint32_t lvl[kBsWords + 4];               // the current level's plane, tile order
     uint32_t wsum[kWarps];                    // zeros of each warp's range
     uint32_t thc[kCols];                      // class counts of the tile (histogram pass)
+    uint8_t wcls[kChunk][kBsWords / 2 + 2 * kCols];   // destination word -> class, per level
     uint32_t tP[kCols + 1];
     uint32_t offq[kCols];                     // class counts of the job before this tile
     uint32_t jP[kCols + 1];
@@ -936,6 +938,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 },
                 [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
             if (lane == 0) sm.wtot[l] = wt;
+            // word -> class map of level l: every nonempty class marks its first
+            // destination word, a running maximum fills the words after it
+            uint8_t *wc = sm.wcls[l];
+            for (uint32_t k = lane; k < wt; k += 32) wc[k] = 0;
+            __syncwarp();
+            for (uint32_t q = lane; q < base; q += 32)
+                if (sm.cnt[base + q]) wc[sm.wpre[base + q]] = (uint8_t)q;
+            __syncwarp();
+            const uint32_t per = (wt + 31) / 32, b0 = lane * per, b1 = min(wt, b0 + per);
+            uint32_t mx = 0;
+            for (uint32_t k = b0; k < b1; ++k) mx = max(mx, (uint32_t)wc[k]);
+            uint32_t inc = mx;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                if (lane >= (uint32_t)d) inc = max(inc, y);
+            }
+            uint32_t run = __shfl_up_sync(kFull, inc, 1);
+            if (lane == 0) run = 0;
+            for (uint32_t k = b0; k < b1; ++k) {
+                run = max(run, (uint32_t)wc[k]);
+                wc[k] = (uint8_t)run;
+            }
         }
         // ---- load and transpose: plane k holds code bit rb-1-k of every symbol
         {
@@ -984,12 +1009,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 const uint32_t wt = sm.wtot[l];
                 uint64_t *lv = t.bv + (uint64_t)(rt.c + l) * t.W;
                 for (uint32_t k = tid; k < wt; k += kThreads) {
-                    uint32_t lo = 0, hi = base;     // last class with wpre <= k
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (sm.wpre[base + mid] <= k) lo = mid; else hi = mid;
-                    }
-                    const uint32_t idx = base + lo;
+                    const uint32_t idx = base + sm.wcls[l][k];
                     const uint64_t gs = sm.glo[idx], ge = gs + sm.cnt[idx];
                     const uint64_t word = (gs >> 6) + (k - sm.wpre[idx]);
                     const uint64_t wb = word << 6;
