@@ -715,18 +715,28 @@ struct BsSmem {
     uint32_t wtot[kChunk + 2];
 };
 
+// x * c as an integer multiply.  The left shifts of the move-vector computation
+// are written this way so that they issue on the multiply-add pipe, which this
+// kernel leaves mostly idle, instead of the integer ALU pipe that bounds it.
+__device__ __forceinline__ uint32_t mul_lo(uint32_t x, uint32_t c)
+{
+    uint32_t r;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(c));
+    return r;
+}
+
 // Move vectors of compress(., m) (Hacker's Delight, Sec. 7-4): the bits that
 // travel 1, 2, 4, 8 and 16 places towards bit 0 in the five rounds.
 __device__ __forceinline__ void compress_moves(uint32_t m, uint32_t mv[5])
 {
-    uint32_t mk = ~m << 1;
+    uint32_t mk = mul_lo(~m, 2u);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        uint32_t mp = mk ^ (mk << 1);
-        mp ^= mp << 2;
-        mp ^= mp << 4;
-        mp ^= mp << 8;
-        mp ^= mp << 16;
+        uint32_t mp = mk ^ mul_lo(mk, 2u);
+        mp ^= mul_lo(mp, 4u);
+        mp ^= mul_lo(mp, 16u);
+        mp ^= mul_lo(mp, 256u);
+        mp ^= mul_lo(mp, 65536u);
         const uint32_t v = mp & m;
         m = (m ^ v) | (v >> (1 << i));
         mv[i] = v;
