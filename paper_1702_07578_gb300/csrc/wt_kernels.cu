@@ -75,6 +75,15 @@ __device__ __forceinline__ RoundText round_text(const TextInfo &t, uint32_t r)
     return x;
 }
 
+// Jobs of the last round of their text with at most kSmallJob symbols are built
+// by one warp each (k_build_small) and get no groups.
+constexpr uint32_t kSmallJob = 1024;
+
+__device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uint64_t n)
+{
+    return n > 0 && n <= kSmallJob && t.L - kChunk * round <= (uint32_t)kChunk;
+}
+
 // The slot owning group g: the last slot whose first group is <= g (slots are
 // in increasing g0 order; empty slots share g0 with their successor).
 __device__ __forceinline__ uint32_t find_slot(const Job *jobs, uint32_t nslots, uint32_t g)
@@ -185,7 +194,7 @@ __global__ void k_root_jobs(RoundArgs a)
     j.off = 0;
     j.text = t;
     j.g0 = 0;
-    j.ng = (uint32_t)((x.n + a.gelems - 1) / a.gelems);
+    j.ng = small_job(x, a.round, x.n) ? 0u : (uint32_t)((x.n + a.gelems - 1) / a.gelems);
     j.tile0 = 0;
     a.jobs[x.slot_base[a.round]] = j;
 }
@@ -215,7 +224,7 @@ __global__ void __launch_bounds__(256) k_child_jobs(RoundArgs a)
     j.off = pj.off + s[q];
     j.text = pj.text;
     j.g0 = 0;
-    j.ng = (cnt + a.gelems - 1) / a.gelems;
+    j.ng = small_job(x, a.round, cnt) ? 0u : (cnt + a.gelems - 1) / a.gelems;
     j.tile0 = 0;
     a.jobs[cb + q] = j;
 }
@@ -1070,10 +1079,176 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Small jobs (at most kSmallJob symbols, last round of their text): one warp
+// builds a whole job with the same bit-sliced splits as k_build_bs, lane i
+// owning word i (symbols 32i .. 32i + 31), with no block-wide barrier.  Wavelet
+// tree rounds >= 1 split every text into one job per prefix (Sec. 2: the
+// independent subtrees), most of them small.
+
+namespace {
+
+constexpr int kSmallWarps = 8;
+
+struct SmallSmem {
+    uint32_t plane[2][kChunk][33];     // current / next planes (+ overflow word)
+    uint32_t lvl[36];                  // the current level's plane
+    uint32_t hist[kCols];              // class counts of the job (leaf level)
+    uint32_t P[kCols + 1];             // prefix sums of hist
+    uint32_t cnt[kCols / 2];           // class counts of the current level
+    uint32_t loc[kCols / 2];           // class start in job order (reversed prefixes)
+    uint32_t glo[kCols / 2];           // class start inside the text's level
+    uint32_t wpre[kCols / 2];          // destination words before each class
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    SmallSmem &sm = reinterpret_cast<SmallSmem *>(smem_raw)[warp];
+    const uint32_t slot = blockIdx.x * kSmallWarps + warp;
+    if (slot >= a.nslots) return;
+    const Job jb = a.jobs[slot];
+    const TextInfo &t = a.texts[jb.text];
+    if (!small_job(t, a.round, jb.n)) return;
+    const RoundText rt = round_text(t, a.round);
+    const uint32_t h = rt.h, rb = rt.rb, n = jb.n;
+    const bool matrix = a.kind == WT_MATRIX;
+    const uint8_t *in = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
+
+    // ---- clear, load and transpose (plane k = code bit rb-1-k), class counts
+    for (uint32_t i = lane; i < 2 * kChunk * 33; i += 32) (&sm.plane[0][0][0])[i] = 0;
+    for (uint32_t i = lane; i < kCols; i += 32) sm.hist[i] = 0;
+    __syncwarp();
+    {
+        uint32_t x[8];
+        load32(in, rt.in_w, 32u * lane, n, x);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t e = 32u * lane + 4u * k + b;
+                if (e < n) atomicAdd(&sm.hist[(x[k] >> (8 * b)) & ((1u << h) - 1u)], 1u);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) transpose8(x[2 * b], x[2 * b + 1]);
+        for (uint32_t k = 0; k < h; ++k) {
+            const uint32_t j = rb - 1u - k;
+            const uint32_t sel = (j & 3u) | ((j & 3u) + 4u) << 4;
+            const bool hi = j >= 4u;
+            const uint32_t t01 = __byte_perm(hi ? x[1] : x[0], hi ? x[3] : x[2], sel);
+            const uint32_t t23 = __byte_perm(hi ? x[5] : x[4], hi ? x[7] : x[6], sel);
+            sm.plane[0][k][lane] = __byte_perm(t01, t23, 0x5410);
+        }
+    }
+    __syncwarp();
+    {
+        const uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.hist[i]; }, [](uint32_t i) { return i; },
+                                           [&](uint32_t i, uint32_t v) { sm.P[i] = v; });
+        if (lane == 0) sm.P[256] = tot;
+    }
+    if (matrix) {                                     // Z[c + l]: zeros of level l, any order
+        for (uint32_t l = 0; l < h; ++l) {
+            uint32_t z = __popc(~sm.plane[0][l][lane]);
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) z += __shfl_xor_sync(kFull, z, d);
+            if (lane == 0) t.zeros[rt.c + l] = z;
+        }
+    }
+    __syncwarp();
+
+    uint64_t *bv = t.bv;
+    for (uint32_t l = 0; l < h; ++l) {
+        uint32_t(*cur)[33] = sm.plane[l & 1];
+        uint32_t(*nxt)[33] = sm.plane[(l + 1) & 1];
+        const uint32_t base = 1u << l, s = h - l;
+        // ---- class tables of level l (fold of the counts; starts in job order
+        //      by reversed prefixes; interval starts in id (WT) / pi_l (WM) order)
+        for (uint32_t q = lane; q < base; q += 32) sm.cnt[q] = sm.P[(q + 1) << s] - sm.P[q << s];
+        __syncwarp();
+        warp_scan_256(base, [&](uint32_t q) { return sm.cnt[q]; }, [&](uint32_t i) { return rev_bits(i, l); },
+                      [&](uint32_t q, uint32_t v) { sm.loc[q] = v; });
+        __syncwarp();
+        if (matrix) {
+            for (uint32_t q = lane; q < base; q += 32) sm.glo[q] = jb.off + sm.loc[q];
+        } else {
+            warp_scan_256(base, [&](uint32_t q) { return sm.cnt[q]; }, [](uint32_t i) { return i; },
+                          [&](uint32_t q, uint32_t v) { sm.glo[q] = jb.off + v; });
+        }
+        __syncwarp();
+        const uint32_t wt = warp_scan_256(
+            base,
+            [&](uint32_t q) {
+                const uint32_t c = sm.cnt[q];
+                if (c == 0) return 0u;
+                const uint32_t gs = sm.glo[q];
+                return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
+            },
+            [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[q] = v; });
+        const uint32_t m0 = cur[l][lane];
+        sm.lvl[lane] = m0;
+        if (lane < 4) sm.lvl[32 + lane] = 0;
+        const uint32_t z0 = __popc(~m0);
+        uint32_t inc = z0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, d);
+            if (lane >= (uint32_t)d) inc += y;
+        }
+        const uint32_t zt = __shfl_sync(kFull, inc, 31), zo = inc - z0;
+        __syncwarp();
+        // ---- copy every class's bits to its interval start in level c + l
+        uint64_t *lv = bv + (uint64_t)(rt.c + l) * t.W;
+        for (uint32_t k = lane; k < wt; k += 32) {
+            uint32_t lo = 0, hi = base;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (sm.wpre[mid] <= k) lo = mid; else hi = mid;
+            }
+            const uint64_t gs = sm.glo[lo], ge = gs + sm.cnt[lo];
+            const uint64_t word = (gs >> 6) + (k - sm.wpre[lo]);
+            const uint64_t wb = word << 6;
+            const uint32_t blo = (uint32_t)((gs > wb ? gs : wb) - wb);
+            uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
+            const uint32_t src = sm.loc[lo] + (uint32_t)(wb + blo - gs);
+            const uint64_t val = extract_bits(sm.lvl, src, bhi - blo) << blo;
+            if (ge == t.n) bhi = 64;
+            if (blo == 0 && bhi == 64) {
+                lv[word] = val;
+            } else {
+                const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
+                atomicAnd(reinterpret_cast<unsigned long long *>(lv + word), ~msk);
+                atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
+            }
+        }
+        // ---- stable split of every later plane by plane l
+        if (l + 1 < h) {
+            uint32_t mz[5], mo[5];
+            compress_moves(~m0, mz);
+            compress_moves(m0, mo);
+            for (uint32_t k = l + 1; k < h; ++k) {
+                const uint32_t x = cur[k][lane];
+                place_bits(nxt[k], zo, compress_apply(x, ~m0, mz), z0);
+                place_bits(nxt[k], zt + 32u * lane - zo, compress_apply(x, m0, mo), 32u - z0);
+                cur[k][lane] = 0;
+            }
+            if (lane == 0)
+                for (uint32_t k = l + 1; k < h; ++k) cur[k][32] = 0;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
 
 cudaError_t configure_kernels()
 {
     cudaError_t e;
+    e = cudaFuncSetAttribute(k_build_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(SmallSmem) * kSmallWarps));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_build_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
@@ -1115,10 +1290,13 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     k_blockscan<<<1, 256, 0, s>>>(a);
     k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
     if (prof) { profile_mark(2, false, s); profile_mark(0, true, s); }
-    if (a.any_plain)
+    if (a.any_plain) {
         k_build_bs<<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+        k_build_small<<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
+                        sizeof(SmallSmem) * kSmallWarps, s>>>(a);
+    }
     if (!a.any_cut) {
-        if (prof) profile_mark(0, false, s, 1);
+        if (prof) profile_mark(0, false, s, 2);
         return cudaGetLastError();
     }
     if (smem_width == 1)
@@ -1127,7 +1305,7 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
         k_build<uint16_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint16_t>), s>>>(a);
     else
         k_build<uint32_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint32_t>), s>>>(a);
-    if (prof) profile_mark(0, false, s, a.any_plain ? 2 : 1);
+    if (prof) profile_mark(0, false, s, a.any_plain ? 3 : 1);
     return cudaGetLastError();
 }
 
