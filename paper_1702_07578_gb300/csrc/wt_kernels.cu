@@ -275,7 +275,7 @@ constexpr int kHistCopies = 2;
 constexpr int kHistStride = kCols + 1;
 constexpr size_t kHistSmem = sizeof(uint32_t) * kHistWarps * kHistCopies * kHistStride;
 
-__global__ void __launch_bounds__(kHistThreads) k_hist(RoundArgs a)
+__global__ void __launch_bounds__(kHistThreads, 3) k_hist(RoundArgs a)
 {
     extern __shared__ __align__(16) uint32_t wh[];
     const uint32_t g = blockIdx.x;
@@ -307,16 +307,26 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(RoundArgs a)
             // bytes: whole 16-byte chunks, range checks on whole words
             const uint4 *v = reinterpret_cast<const uint4 *>(lo);
             const uint64_t nchunks = (uint64_t)(hi - lo) >> 4;
-            for (uint64_t k = threadIdx.x; k < nchunks; k += kHistThreads) {
-                const uint4 q = __ldg(v + k);
-                const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+            // four 16-byte loads in flight per thread before their counts
+            for (uint64_t k0 = threadIdx.x; k0 < nchunks; k0 += 4 * kHistThreads) {
+                uint4 q[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t x = words[j];
-                    bad |= (x & top4) != 0u;
-                    if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
+                for (int u = 0; u < 4; ++u) {
+                    const uint64_t k = k0 + (uint64_t)u * kHistThreads;
+                    q[u] = k < nchunks ? __ldg(v + k) : make_uint4(0u, 0u, 0u, 0u);
+                }
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) atomicAdd(&mine[((x >> (8 * b + shift)) & mask)], 1u);
+                for (int u = 0; u < 4; ++u) {
+                    if (k0 + (uint64_t)u * kHistThreads >= nchunks) break;
+                    const uint32_t words[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t x = words[j];
+                        bad |= (x & top4) != 0u;
+                        if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) atomicAdd(&mine[((x >> (8 * b + shift)) & mask)], 1u);
+                    }
                 }
             }
             for (uint64_t i = i0 + nchunks * 16 + threadIdx.x; i < i1; i += kHistThreads) {
