@@ -746,6 +746,15 @@ __device__ __forceinline__ uint32_t mul_lo(uint32_t x, uint32_t c)
 
 // Move vectors of compress(., m) (Hacker's Delight, Sec. 7-4): the bits that
 // travel 1, 2, 4, 8 and 16 places towards bit 0 in the five rounds.
+// x >> s (1 <= s <= 31) as the high word of x * 2^(32-s): a multiply, so that it
+// issues on the multiply-add pipe instead of the integer ALU pipe.
+__device__ __forceinline__ uint32_t shr_hi(uint32_t x, uint32_t s)
+{
+    uint32_t r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(1u << (32 - s)));
+    return r;
+}
+
 __device__ __forceinline__ void compress_moves(uint32_t m, uint32_t mv[5])
 {
     uint32_t mk = mul_lo(~m, 2u);
@@ -757,21 +766,24 @@ __device__ __forceinline__ void compress_moves(uint32_t m, uint32_t mv[5])
         mp ^= mul_lo(mp, 256u);
         mp ^= mul_lo(mp, 65536u);
         const uint32_t v = mp & m;
-        m = (m ^ v) | (v >> (1 << i));
-        mv[i] = v;
+        const uint32_t vs = shr_hi(v, 1u << i);
+        m = (m ^ v) | vs;
+        mv[i] = vs;                 // receive mask of round i: positions a bit arrives at
         mk &= ~mp;
     }
 }
 
-__device__ __forceinline__ uint32_t compress_apply(uint32_t x, uint32_t m, const uint32_t mv[5])
+// compress with receive masks: each round takes at every receiving position the
+// bit from 2^i places up; stale copies stay outside [0, popc(m)) and `keep`
+// (popc(m) low bits) removes them.
+__device__ __forceinline__ uint32_t compress_apply(uint32_t x, uint32_t keep, const uint32_t mvs[5])
 {
-    x &= m;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const uint32_t t = x & mv[i];
-        x = (x ^ t) | (t >> (1 << i));
+        const uint32_t y = shr_hi(x, 1u << i);
+        x = (y & mvs[i]) | (x & ~mvs[i]);
     }
-    return x;
+    return x & keep;
 }
 
 // OR the low `len` (<= 64) bits of `part` into a plane at bit offset d.
@@ -1066,12 +1078,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 compress_moves(m1, mo1);
                 const uint32_t dz = zo, d1 = zt + w0 * 32u - zo;
                 const uint32_t nz = z0 + z1, no = 64u - nz;
+                const uint32_t kz0 = z0 == 32u ? ~0u : (1u << z0) - 1u;
+                const uint32_t ko0 = z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u;
+                const uint32_t kz1 = z1 == 32u ? ~0u : (1u << z1) - 1u;
+                const uint32_t ko1 = z1 == 0u ? ~0u : (1u << (32u - z1)) - 1u;
                 for (uint32_t k = l + 1; k < h; ++k) {
                     const uint32_t x0 = cur[k][w0], x1 = cur[k][w0 + 1];
-                    const uint64_t pz = (uint64_t)compress_apply(x0, ~m0, mz0) |
-                                        ((uint64_t)compress_apply(x1, ~m1, mz1) << z0);
-                    const uint64_t po = (uint64_t)compress_apply(x0, m0, mo0) |
-                                        ((uint64_t)compress_apply(x1, m1, mo1) << (32u - z0));
+                    const uint64_t pz = (uint64_t)compress_apply(x0, kz0, mz0) |
+                                        ((uint64_t)compress_apply(x1, kz1, mz1) << z0);
+                    const uint64_t po = (uint64_t)compress_apply(x0, ko0, mo0) |
+                                        ((uint64_t)compress_apply(x1, ko1, mo1) << (32u - z0));
                     place_bits(nxt[k], dz, pz, nz);
                     place_bits(nxt[k], d1, po, no);
                     cur[k][w0] = 0;
@@ -1240,8 +1256,9 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
             compress_moves(m0, mo);
             for (uint32_t k = l + 1; k < h; ++k) {
                 const uint32_t x = cur[k][lane];
-                place_bits(nxt[k], zo, compress_apply(x, ~m0, mz), z0);
-                place_bits(nxt[k], zt + 32u * lane - zo, compress_apply(x, m0, mo), 32u - z0);
+                place_bits(nxt[k], zo, compress_apply(x, z0 == 32u ? ~0u : (1u << z0) - 1u, mz), z0);
+                place_bits(nxt[k], zt + 32u * lane - zo,
+                           compress_apply(x, z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u, mo), 32u - z0);
                 cur[k][lane] = 0;
             }
             if (lane == 0)
