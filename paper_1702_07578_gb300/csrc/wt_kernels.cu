@@ -744,8 +744,6 @@ __device__ __forceinline__ uint32_t mul_lo(uint32_t x, uint32_t c)
     return r;
 }
 
-// Move vectors of compress(., m) (Hacker's Delight, Sec. 7-4): the bits that
-// travel 1, 2, 4, 8 and 16 places towards bit 0 in the five rounds.
 // x >> s (1 <= s <= 31) as the high word of x * 2^(32-s): a multiply, so that it
 // issues on the multiply-add pipe instead of the integer ALU pipe.
 __device__ __forceinline__ uint32_t shr_hi(uint32_t x, uint32_t s)
@@ -755,6 +753,8 @@ __device__ __forceinline__ uint32_t shr_hi(uint32_t x, uint32_t s)
     return r;
 }
 
+// Masks of compress(., m) (Hacker's Delight, Sec. 7-4): in round i (i = 0..4)
+// bits travel 2^i places towards bit 0; mv[i] holds the positions they arrive at.
 __device__ __forceinline__ void compress_moves(uint32_t m, uint32_t mv[5])
 {
     uint32_t mk = mul_lo(~m, 2u);
