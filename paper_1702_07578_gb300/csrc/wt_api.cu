@@ -103,7 +103,7 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
     for (uint32_t r = 0; r < p.rounds; ++r) {
         if (slot_acc[r] >= (1ull << 31)) return WT_ERR_INVALID_ARG;
         p.width[r] = width[r] ? width[r] : 1;
-        p.gelems[r] = spb ? spb : (uint32_t)group_elems(p.width[r]);
+        p.gelems[r] = spb ? spb : kDefaultGroup;
         const uint64_t ge = p.gelems[r];
         for (uint32_t i = 0; i < count; ++i) {
             const TextInfo &ti = p.texts[i];

@@ -22,16 +22,13 @@ constexpr int kMaxRounds = 4;         // L <= 32
 constexpr int kChunk = 8;             // levels per round
 constexpr int kThreads = 512;         // build / histogram block size
 constexpr int kWarps = kThreads / 32;
-constexpr int kTilesPerGroup = 4;     // tiles one build block processes
 constexpr int kRowsPerBlock = 64;     // groups per block of the segmented scan
 constexpr int kCols = 256;            // histogram columns (2^8 classes per round)
 constexpr int kMaxTreeSigmaLog = 24;  // WT alphabets up to 2^24
 constexpr int kTileSyms = 32768;      // symbols per tile of the bit-sliced build; groups are multiples
 
-// Elements per thread and tile size, by the width of an element in shared memory.
-__host__ __device__ constexpr int elems_per_thread(int width) { return width == 1 ? 32 : 16; }
-__host__ __device__ constexpr int tile_elems(int width) { return kThreads * elems_per_thread(width); }
-__host__ __device__ constexpr int group_elems(int width) { return tile_elems(width) * kTilesPerGroup; }
+// Default symbols per build block: two tiles.
+constexpr uint32_t kDefaultGroup = 2 * 32768;
 
 // Smallest storage width (bytes) that holds b-bit codes.
 __host__ __device__ inline uint32_t width_for_bits(uint32_t b) { return b <= 8 ? 1u : (b <= 16 ? 2u : 4u); }

@@ -77,11 +77,25 @@ __device__ __forceinline__ RoundText round_text(const TextInfo &t, uint32_t r)
 
 // Jobs of the last round of their text with at most kSmallJob symbols are built
 // by one warp each (k_build_small) and get no groups.
-constexpr uint32_t kSmallJob = 1024;
+constexpr uint32_t kSmallWords = 4;                  // words per lane of the warp build
+constexpr uint32_t kSmallJob = 32 * 32 * kSmallWords;   // 4096 symbols
 
 __device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uint64_t n)
 {
     return n > 0 && n <= kSmallJob && t.L - kChunk * round <= (uint32_t)kChunk;
+}
+
+// Lanes whose 8-bit key equals this lane's, among the lanes with ok set: the AND
+// of eight bit ballots (a warp multisplit), all lanes taking part.
+__device__ __forceinline__ uint32_t peers8(uint32_t key, bool ok)
+{
+    uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t b = __ballot_sync(0xffffffffu, (key >> k) & 1u);
+        peers &= ((key >> k) & 1u) ? b : ~b;
+    }
+    return peers;
 }
 
 // The slot owning group g: the last slot whose first group is <= g (slots are
@@ -230,37 +244,55 @@ __global__ void __launch_bounds__(256) k_child_jobs(RoundArgs a)
 }
 
 // Exclusive scans over all slots of the group counts -> g0 (total groups) and
-// of the tile counts -> tile0.
+// of the tile counts -> tile0, in chunks of 4096 slots (4 per thread).
 __global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
 {
-    __shared__ uint32_t part[1024], tpart[1024];
-    const uint32_t n = a.nslots;
-    const uint32_t per = (n + 1023) / 1024;
-    const uint32_t b = threadIdx.x * per, e = min(n, b + per);
-    uint32_t sum = 0, tsum = 0;
-    for (uint32_t i = b; i < e; ++i) {
-        sum += a.jobs[i].ng;
-        tsum += (a.jobs[i].n + kTileSyms - 1) / kTileSyms;
-    }
-    part[threadIdx.x] = sum;
-    tpart[threadIdx.x] = tsum;
-    __syncthreads();
-    for (uint32_t d = 1; d < 1024; d <<= 1) {
-        const uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
-        const uint32_t tv = threadIdx.x >= d ? tpart[threadIdx.x - d] : 0u;
+    __shared__ uint32_t wg[32], wt[32];
+    const uint32_t n = a.nslots, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    uint32_t carry_g = 0, carry_t = 0;
+    for (uint32_t c0 = 0; c0 < n; c0 += 4096) {
+        uint32_t ng[4], nt[4], sg = 0, st = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t i = c0 + 4u * tid + j;
+            ng[j] = i < n ? a.jobs[i].ng : 0u;
+            nt[j] = i < n ? (a.jobs[i].n + kTileSyms - 1) / kTileSyms : 0u;
+            sg += ng[j];
+            st += nt[j];
+        }
+        uint32_t ig = sg, it = st;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t yg = __shfl_up_sync(kFull, ig, d), yt = __shfl_up_sync(kFull, it, d);
+            if (lane >= (uint32_t)d) { ig += yg; it += yt; }
+        }
+        if (lane == 31) { wg[warp] = ig; wt[warp] = it; }
         __syncthreads();
-        part[threadIdx.x] += v;
-        tpart[threadIdx.x] += tv;
+        const uint32_t xg = wg[lane], xt = wt[lane];
+        uint32_t pg = xg, pt = xt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t yg = __shfl_up_sync(kFull, pg, d), yt = __shfl_up_sync(kFull, pt, d);
+            if (lane >= (uint32_t)d) { pg += yg; pt += yt; }
+        }
+        const uint32_t tg = __shfl_sync(kFull, pg, 31), tt = __shfl_sync(kFull, pt, 31);
+        uint32_t rg = carry_g + __shfl_sync(kFull, pg - xg, warp) + ig - sg;
+        uint32_t rt_ = carry_t + __shfl_sync(kFull, pt - xt, warp) + it - st;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t i = c0 + 4u * tid + j;
+            if (i < n) {
+                a.jobs[i].g0 = rg;
+                a.jobs[i].tile0 = rt_;
+            }
+            rg += ng[j];
+            rt_ += nt[j];
+        }
+        carry_g += tg;
+        carry_t += tt;
         __syncthreads();
     }
-    uint32_t run = part[threadIdx.x] - sum, trun = tpart[threadIdx.x] - tsum;
-    for (uint32_t i = b; i < e; ++i) {
-        a.jobs[i].g0 = run;
-        a.jobs[i].tile0 = trun;
-        run += a.jobs[i].ng;
-        trun += (a.jobs[i].n + kTileSyms - 1) / kTileSyms;
-    }
-    if (threadIdx.x == 1023) a.ctl->total_groups[a.round] = part[1023];
+    if (tid == 0) a.ctl->total_groups[a.round] = carry_g;
 }
 
 // ---------------------------------------------------------------------------
@@ -436,34 +468,12 @@ __global__ void __launch_bounds__(256) k_groupexcl(RoundArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// a2, a4, a5: interval starts, stable splits, packed bit writes, re-sorted symbols
+// a2, a4, a5: shared pieces of the build kernels
 
 namespace {
 
 // Heap layout of per-level class tables: entry (1 << l) + q for class q of level l.
 constexpr int kHeap = 512;
-
-template <typename E>
-struct BuildSmem {
-    static constexpr int R = elems_per_thread(sizeof(E));
-    static constexpr int S = tile_elems(sizeof(E));
-    E buf[2][S];
-    uint32_t lvl[S / 32 + 4];          // packed bits of the current level, tile order
-    uint32_t whist[kWarps][kCols];     // per-warp class counts of the tile
-    uint32_t thist[kCols];             // class counts of the tile
-    uint32_t offq[kCols];              // class counts of the job before this tile
-    uint32_t jP[kCols + 1];            // prefix sums (job totals, tile counts, offsets)
-    uint32_t tP[kCols + 1];
-    uint32_t oP[kCols + 1];
-    uint32_t jcnt[kHeap];              // job class totals per level
-    uint32_t jspos[kHeap];             // interval starts inside the job per level
-    uint32_t tcnt[kHeap];              // tile class counts per level
-    uint32_t loc[kHeap];               // class start inside the tile (tile order)
-    uint32_t glo[kHeap];               // class start inside the text's level (bits)
-    uint32_t wpre[kHeap];              // prefix of destination words per level
-    uint32_t wtot[kChunk + 2];
-    uint32_t wones[kWarps];
-};
 
 // Up to 64 bits of the tile's packed level starting at bit p.
 __device__ __forceinline__ uint64_t extract_bits(const uint32_t *lvl, uint32_t p, uint32_t k)
@@ -477,226 +487,6 @@ __device__ __forceinline__ uint64_t extract_bits(const uint32_t *lvl, uint32_t p
 }
 
 }  // namespace
-
-template <typename E>
-__global__ void __launch_bounds__(kThreads, 2) k_build(RoundArgs a)
-{
-    using SM = BuildSmem<E>;
-    constexpr int R = SM::R;
-    constexpr int S = SM::S;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    SM &sm = *reinterpret_cast<SM *>(smem_raw);
-
-    const uint32_t g = blockIdx.x;
-    if (g >= a.ctl->total_groups[a.round]) return;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t slot = find_slot(a.jobs, a.nslots, g);
-    const Job jb = a.jobs[slot];
-    const TextInfo &t = a.texts[jb.text];
-    const RoundText rt = round_text(t, a.round);
-    const uint32_t h = rt.h, rb = rt.rb;
-    const uint32_t gi = g - jb.g0;
-    const bool matrix = a.kind == WT_MATRIX;
-    const bool has_cut = rt.cut != nullptr;
-    if (!has_cut) return;                            // rounds without a cut: k_build_bs
-
-    // job totals -> per-level class totals and interval starts (fold, Alg. 1;
-    // zero-based prefix sum in id or pi_l order, Sec. 3.1 / 5.1)
-    for (uint32_t q = tid; q < kCols; q += kThreads) {
-        sm.thist[q] = a.jobhist[(size_t)slot * kCols + q];
-        sm.offq[q] = a.gexcl[(size_t)g * kCols + q];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.thist[i]; },
-                                     [](uint32_t i) { return i; },
-                                     [&](uint32_t i, uint32_t v) { sm.jP[i] = v; });
-        if (lane == 0) sm.jP[256] = tot;
-    }
-    __syncthreads();
-    for (uint32_t idx = tid; idx < kHeap; idx += kThreads) {
-        if (idx == 0) continue;
-        uint32_t l = 31u - __clz(idx), q = idx - (1u << l);
-        if (l <= h) {
-            uint32_t s = h - l;
-            sm.jcnt[idx] = sm.jP[(q + 1) << s] - sm.jP[q << s];
-        }
-    }
-    __syncthreads();
-    if (warp <= h) {
-        const uint32_t l = warp, base = 1u << l;
-        warp_scan_256(base, [&](uint32_t q) { return sm.jcnt[base + q]; },
-                      [&](uint32_t i) { return matrix ? rev_bits(i, l) : i; },
-                      [&](uint32_t q, uint32_t v) { sm.jspos[base + q] = v; });
-    }
-    if (matrix && gi == 0 && tid < h) {        // Z[c + l]: even (l+1)-prefixes
-        const uint32_t l = tid, base = 2u << l;
-        uint32_t z = 0;
-        for (uint32_t p = 0; p < base; p += 2) z += sm.jcnt[base + p];
-        t.zeros[rt.c + l] = z;
-    }
-    __syncthreads();
-
-    const uint64_t g_begin = (uint64_t)gi * a.gelems;
-    const uint64_t g_end = min((uint64_t)jb.n, g_begin + a.gelems);
-    const uint8_t *in_base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
-    const uint32_t shift = rb - h, cmask = (1u << h) - 1u;
-
-    for (uint64_t t0 = g_begin; t0 < g_end; t0 += S) {
-        const uint32_t m = (uint32_t)min((uint64_t)S, g_end - t0);
-        // ---- load the tile (text order) and count its classes
-        for (uint32_t i = tid; i < kWarps * kCols; i += kThreads) (&sm.whist[0][0])[i] = 0;
-        __syncthreads();
-        {
-            uint32_t *mine = sm.whist[warp];
-            E *dst = sm.buf[0];
-            for_range(in_base, rt.in_w, t0, t0 + m, [&](uint32_t li, uint32_t v) {
-                dst[li] = static_cast<E>(v);
-                atomicAdd(&mine[(v >> shift) & cmask], 1u);
-            });
-        }
-        __syncthreads();
-        for (uint32_t q = tid; q < kCols; q += kThreads) {
-            uint32_t s = 0;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) s += sm.whist[w][q];
-            sm.thist[q] = s;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.thist[i]; },
-                                         [](uint32_t i) { return i; },
-                                         [&](uint32_t i, uint32_t v) { sm.tP[i] = v; });
-            if (lane == 0) sm.tP[256] = tot;
-        } else if (warp == 1) {
-            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.offq[i]; },
-                                         [](uint32_t i) { return i; },
-                                         [&](uint32_t i, uint32_t v) { sm.oP[i] = v; });
-            if (lane == 0) sm.oP[256] = tot;
-        }
-        __syncthreads();
-        for (uint32_t idx = tid; idx < kHeap; idx += kThreads) {
-            if (idx == 0) continue;
-            uint32_t l = 31u - __clz(idx), q = idx - (1u << l);
-            if (l <= h) {
-                uint32_t s = h - l, lo = q << s, hi = (q + 1) << s;
-                sm.tcnt[idx] = sm.tP[hi] - sm.tP[lo];
-                sm.glo[idx] = jb.off + sm.jspos[idx] + (sm.oP[hi] - sm.oP[lo]);
-            }
-        }
-        __syncthreads();
-        if (warp <= h) {
-            const uint32_t l = warp, base = 1u << l;
-            // tile order after l splits: classes by reversed prefix
-            warp_scan_256(base, [&](uint32_t q) { return sm.tcnt[base + q]; },
-                          [&](uint32_t i) { return rev_bits(i, l); },
-                          [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
-            uint32_t wt = warp_scan_256(
-                base,
-                [&](uint32_t q) {
-                    uint32_t c = sm.tcnt[base + q];
-                    if (c == 0) return 0u;
-                    uint32_t s = sm.glo[base + q];
-                    return ((s + c - 1) >> 6) - (s >> 6) + 1u;
-                },
-                [](uint32_t i) { return i; },
-                [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
-            if (lane == 0) sm.wtot[l] = wt;
-        } else if (warp == kWarps - 1) {
-            for (uint32_t q = lane; q < kCols; q += 32) sm.offq[q] += sm.thist[q];
-        }
-        __syncthreads();
-
-        // ---- levels of this round
-        for (uint32_t l = 0; l < h; ++l) {
-            const E *cur = sm.buf[l & 1];
-            E *nxt = sm.buf[(l + 1) & 1];
-            const uint32_t sh = rb - 1u - l;
-            uint32_t e[R];
-            uint32_t ones = 0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                uint32_t idx = (warp * R + r) * 32u + lane;
-                uint32_t v = idx < m ? (uint32_t)cur[idx] : 0u;
-                e[r] = v;
-                uint32_t B = __ballot_sync(kFull, (v >> sh) & 1u);
-                if (lane == 0) sm.lvl[warp * R + r] = B;
-                ones += __popc(B);
-            }
-            if (lane == 0) sm.wones[warp] = ones;
-            __syncthreads();
-
-            // copy every class's bits to its interval start in level c + l
-            {
-                const uint32_t base = 1u << l, wt = sm.wtot[l];
-                uint64_t *lv = t.bv + (uint64_t)(rt.c + l) * t.W;
-                for (uint32_t k = tid; k < wt; k += kThreads) {
-                    uint32_t lo = 0, hi = base;     // last class with wpre <= k
-                    while (hi - lo > 1) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if (sm.wpre[base + mid] <= k) lo = mid; else hi = mid;
-                    }
-                    const uint32_t idx = base + lo;
-                    const uint64_t gs = sm.glo[idx], ge = gs + sm.tcnt[idx];
-                    const uint64_t word = (gs >> 6) + (k - sm.wpre[idx]);
-                    const uint64_t wb = word << 6;
-                    const uint32_t blo = (uint32_t)((gs > wb ? gs : wb) - wb);
-                    uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
-                    const uint32_t src = sm.loc[idx] + (uint32_t)(wb + blo - gs);
-                    const uint64_t val = extract_bits(sm.lvl, src, bhi - blo) << blo;
-                    if (ge == t.n) bhi = 64;       // bits past n belong to the last interval
-                    if (blo == 0 && bhi == 64) {
-                        lv[word] = val;
-                    } else {
-                        const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
-                        atomicAnd(reinterpret_cast<unsigned long long *>(lv + word), ~msk);
-                        atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
-                    }
-                }
-            }
-
-            if (l + 1 < h || has_cut) {
-                // stable split by bit l: zeros keep their order first, then ones
-                uint32_t x = lane < (uint32_t)kWarps ? sm.wones[lane] : 0u;
-                uint32_t inc = x;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    uint32_t y = __shfl_up_sync(kFull, inc, d);
-                    if (lane >= (uint32_t)d) inc += y;
-                }
-                const uint32_t total = __shfl_sync(kFull, inc, kWarps - 1);
-                uint32_t run = warp ? __shfl_sync(kFull, inc, warp - 1) : 0u;
-                const uint32_t zt = m - total;
-                const uint32_t lt = lanemask_lt();
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t idx = (warp * R + r) * 32u + lane;
-                    const uint32_t B = sm.lvl[warp * R + r];
-                    const uint32_t rk = run + __popc(B & lt);
-                    const uint32_t pos = ((e[r] >> sh) & 1u) ? zt + rk : idx - rk;
-                    if (idx < m) nxt[pos] = static_cast<E>(e[r]);
-                    run += __popc(B);
-                }
-            }
-            __syncthreads();
-        }
-
-        // ---- re-sorted symbols for the next round (stable counting sort by the
-        //      round's 8-bit class, Alg. 2; WM: reversed order, Obs. 2)
-        if (has_cut) {
-            const E *fin = sm.buf[h & 1];
-            const uint32_t base = 1u << h;
-            const uint32_t low = (1u << (rb - h)) - 1u;
-            for (uint32_t i = tid; i < m; i += kThreads) {
-                const uint32_t v = fin[i];
-                const uint32_t idx = base + ((v >> shift) & cmask);
-                const uint64_t dst = (uint64_t)sm.glo[idx] + (i - sm.loc[idx]);
-                store_sym(rt.cut, rt.cut_w, dst, v & low);
-            }
-            __syncthreads();
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Bit-sliced variant of a2-a4 for rounds without a cut (every text with sigma
@@ -720,6 +510,7 @@ struct BsSmem {
     uint32_t lvl[kBsWords + 4];               // the current level's plane, tile order
     uint32_t wsum[kWarps];                    // zeros of each warp's range
     uint32_t thc[kCols];                      // class counts of the tile (histogram pass)
+    uint16_t cntw[kWarps][kCols];             // cut: class counts / offsets per warp chunk
     uint8_t wcls[kChunk][kBsWords / 2 + 2 * kCols];   // destination word -> class, per level
     uint32_t tP[kCols + 1];
     uint32_t offq[kCols];                     // class counts of the job before this tile
@@ -809,20 +600,12 @@ __device__ __forceinline__ void transpose8(uint32_t &lo, uint32_t &hi)
     t = (lo ^ (hi << 4)) & 0xF0F0F0F0u; lo = lo ^ t; hi = hi ^ (t >> 4);
 }
 
-// Low bytes of 4 consecutive symbols of width w (2 or 4) packed into one word.
-__device__ __forceinline__ uint32_t pack4(const uint4 &v, int half, uint32_t w)
-{
-    if (w == 2) {
-        const uint32_t a = half ? v.z : v.x, b = half ? v.w : v.y;
-        return __byte_perm(a, b, 0x6420);
-    }
-    return __byte_perm(__byte_perm(v.x, v.y, 0x0040), __byte_perm(v.z, v.w, 0x0040), 0x5410);
-}
-
-// Symbols [e0, e0 + 32) of the tile as 8 words of 4 bytes (the low byte of each
-// symbol); symbols at or beyond m read as 0xff, all ones, so that padding stays
-// at the end of every stable split.
-__device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t e0, uint32_t m, uint32_t x[8])
+// Symbols [e0, e0 + 32) of the tile as 8 words of 4 bytes, byte = bits
+// [shift, shift + 8) of the symbol (its round's 8 top code bits, or all of them
+// when it has fewer); symbols at or beyond m read as 0xff, all ones, so that
+// padding stays at the end of every stable split.
+__device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t e0, uint32_t m, uint32_t shift,
+                                       uint32_t x[8])
 {
     const uint8_t *p = tile + (size_t)e0 * w;
     if (e0 + 32u <= m && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
@@ -835,12 +618,25 @@ __device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint4 a = __ldg(q + k);
-                x[2 * k] = pack4(a, 0, 2);
-                x[2 * k + 1] = pack4(a, 1, 2);
+                const uint32_t v[4] = {a.x, a.y, a.z, a.w};
+                uint32_t lo = 0, hi = 0;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    lo |= ((v[j] >> shift) & 0xffu) << (16 * j);
+                    lo |= ((v[j] >> (16 + shift)) & 0xffu) << (16 * j + 8);
+                    hi |= ((v[2 + j] >> shift) & 0xffu) << (16 * j);
+                    hi |= ((v[2 + j] >> (16 + shift)) & 0xffu) << (16 * j + 8);
+                }
+                x[2 * k] = lo;
+                x[2 * k + 1] = hi;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) x[k] = pack4(__ldg(q + k), 0, 4);
+            for (int k = 0; k < 8; ++k) {
+                const uint4 a = __ldg(q + k);
+                x[k] = ((a.x >> shift) & 0xffu) | ((a.y >> shift) & 0xffu) << 8 |
+                       ((a.z >> shift) & 0xffu) << 16 | ((a.w >> shift) & 0xffu) << 24;
+            }
         }
         return;
     }
@@ -850,7 +646,7 @@ __device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const uint32_t e = e0 + 4u * k + b;
-            const uint32_t v = e < m ? (load_sym(tile, w, e) & 0xffu) : 0xffu;
+            const uint32_t v = e < m ? ((load_sym(tile, w, e) >> shift) & 0xffu) : 0xffu;
             word |= v << (8 * b);
         }
         x[k] = word;
@@ -887,8 +683,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const Job jb = a.jobs[slot];
     const TextInfo &t = a.texts[jb.text];
     const RoundText rt = round_text(t, a.round);
-    if (rt.cut != nullptr) return;                   // rounds with a cut: k_build
-    const uint32_t h = rt.h, rb = rt.rb;             // rb == h here
+    const uint32_t h = rt.h, rb = rt.rb;
+    const uint32_t shift = rb - h;                   // > 0 in rounds with a cut
     const uint32_t gi = g - jb.g0;
     const bool matrix = a.kind == WT_MATRIX;
 
@@ -964,6 +760,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         __syncthreads();
         // per level (one warp each): class starts in tile order (reversed
         // prefixes, Obs. 2) and destination words of every class
+        if (warp == h && rt.cut != nullptr) {       // class starts after the last split (cut)
+            const uint32_t base = 1u << h;
+            warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
+                          [&](uint32_t i) { return rev_bits(i, h); },
+                          [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
+        }
         if (warp < h) {
             const uint32_t l = warp, base = 1u << l;
             warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
@@ -1007,10 +809,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         {
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             uint32_t x[8];
-            load32(tile, rt.in_w, 32u * w0, m, x);
-            store_planes(x, rb, h, sm.plane[0], w0);
-            load32(tile, rt.in_w, 32u * w0 + 32u, m, x);
-            store_planes(x, rb, h, sm.plane[0], w0 + 1);
+            load32(tile, rt.in_w, 32u * w0, m, shift, x);
+            store_planes(x, h, h, sm.plane[0], w0);
+            load32(tile, rt.in_w, 32u * w0 + 32u, m, shift, x);
+            store_planes(x, h, h, sm.plane[0], w0 + 1);
         }
         __syncthreads();
 
@@ -1098,6 +900,77 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             }
             __syncthreads();
         }
+        // ---- re-sorted symbols for the next round: the tile stably sorted by its
+        //      8-bit class (the counting sort of Alg. 2), each class's run written
+        //      at its interval start of level h (id order for the WT, reversed for
+        //      the WM, Obs. 2); only the low rb - h bits go on.  Ranks: warp w
+        //      takes symbols [2048w, 2048w + 2048) in text order, equal classes
+        //      within a step are ranked by lane, chunks by a scan over warps.  The
+        //      values are staged in sorted order in the (now idle) plane buffers
+        //      so that every class run is written with consecutive stores.
+        if (rt.cut != nullptr) {
+            constexpr uint32_t kPer = kBsTile / kWarps;
+            const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
+            const uint32_t low = (1u << shift) - 1u;
+            const uint32_t e_end = min(m, warp * kPer + kPer);
+            const uint32_t base_h = 1u << h;
+            uint16_t *cw = sm.cntw[warp];
+            uint8_t *stage8 = reinterpret_cast<uint8_t *>(&sm.plane[0][0][0]);
+            uint16_t *stage16 = reinterpret_cast<uint16_t *>(&sm.plane[0][0][0]);
+            const bool staged = rt.cut_w <= 2;        // 32768 values fit the plane buffers
+            for (uint32_t q = lane; q < kCols; q += 32) cw[q] = 0;
+            __syncwarp();
+            for (uint32_t e0 = warp * kPer; e0 < e_end; e0 += 32) {
+                const uint32_t e = e0 + lane;
+                const bool ok = e < e_end;
+                const uint32_t v = ok ? load_sym(tile, rt.in_w, e) : 0u;
+                const uint32_t q = ok ? (v >> shift) & 0xffu : 0u;
+                const uint32_t peers = peers8(q, ok);
+                if (ok && (peers >> lane) == 1u) cw[q] = (uint16_t)(cw[q] + __popc(peers));
+                __syncwarp();
+            }
+            __syncthreads();
+            for (uint32_t q = tid; q < kCols; q += kThreads) {
+                uint32_t run = 0;
+                for (int w = 0; w < kWarps; ++w) {
+                    const uint32_t c = sm.cntw[w][q];
+                    sm.cntw[w][q] = (uint16_t)run;
+                    run += c;
+                }
+            }
+            __syncthreads();
+            const uint32_t lt = lanemask_lt();
+            for (uint32_t e0 = warp * kPer; e0 < e_end; e0 += 32) {
+                const uint32_t e = e0 + lane;
+                const bool ok = e < e_end;
+                const uint32_t v = ok ? load_sym(tile, rt.in_w, e) : 0u;
+                const uint32_t q = ok ? (v >> shift) & 0xffu : 0u;
+                const uint32_t peers = peers8(q, ok);
+                const uint32_t rank = ok ? cw[q] + __popc(peers & lt) : 0u;
+                __syncwarp();
+                if (ok) {
+                    if ((peers >> lane) == 1u) cw[q] = (uint16_t)(rank + 1u);
+                    if (!staged) {
+                        store_sym(rt.cut, rt.cut_w, (uint64_t)sm.glo[base_h + q] + rank, v & low);
+                    } else {
+                        const uint32_t pos = sm.loc[base_h + q] + rank;      // place in the sorted tile
+                        if (rt.cut_w == 1) stage8[pos] = (uint8_t)(v & low);
+                        else stage16[pos] = (uint16_t)(v & low);
+                    }
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            if (staged) {                               // class runs, one warp per class
+                for (uint32_t q = warp; q < base_h; q += kWarps) {
+                    const uint32_t c = sm.cnt[base_h + q], src = sm.loc[base_h + q];
+                    const uint64_t dst = sm.glo[base_h + q];
+                    for (uint32_t i = lane; i < c; i += 32)
+                        store_sym(rt.cut, rt.cut_w, dst + i, rt.cut_w == 1 ? stage8[src + i] : stage16[src + i]);
+                }
+                __syncthreads();
+            }
+        }
         // leaf counts of this tile advance the job offsets for the next tile
         for (uint32_t q = tid; q < (1u << h); q += kThreads) sm.offq[q] += sm.cnt[(1u << h) + q];
         __syncthreads();
@@ -1116,8 +989,8 @@ namespace {
 constexpr int kSmallWarps = 8;
 
 struct SmallSmem {
-    uint32_t plane[2][kChunk][33];     // current / next planes (+ overflow word)
-    uint32_t lvl[36];                  // the current level's plane
+    uint32_t plane[2][kChunk][32 * kSmallWords + 1];   // current / next planes (+ overflow word)
+    uint32_t lvl[32 * kSmallWords + 4];                // the current level's plane
     uint32_t hist[kCols];              // class counts of the job (leaf level)
     uint32_t P[kCols + 1];             // prefix sums of hist
     uint32_t cnt[kCols / 2];           // class counts of the current level
@@ -1130,6 +1003,7 @@ struct SmallSmem {
 
 __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
 {
+    constexpr uint32_t KW = kSmallWords, NW = 32 * kSmallWords;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     SmallSmem &sm = reinterpret_cast<SmallSmem *>(smem_raw)[warp];
@@ -1142,31 +1016,32 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
     const uint32_t h = rt.h, rb = rt.rb, n = jb.n;
     const bool matrix = a.kind == WT_MATRIX;
     const uint8_t *in = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
+    const uint32_t w0 = KW * lane;                    // this lane's words: w0 .. w0 + KW - 1
 
     // ---- clear, load and transpose (plane k = code bit rb-1-k), class counts
-    for (uint32_t i = lane; i < 2 * kChunk * 33; i += 32) (&sm.plane[0][0][0])[i] = 0;
+    for (uint32_t i = lane; i < 2 * kChunk * (NW + 1); i += 32) (&sm.plane[0][0][0])[i] = 0;
     for (uint32_t i = lane; i < kCols; i += 32) sm.hist[i] = 0;
     __syncwarp();
-    {
+    for (uint32_t j = 0; j < KW; ++j) {
         uint32_t x[8];
-        load32(in, rt.in_w, 32u * lane, n, x);
+        load32(in, rt.in_w, 32u * (w0 + j), n, 0u, x);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const uint32_t e = 32u * lane + 4u * k + b;
+                const uint32_t e = 32u * (w0 + j) + 4u * k + b;
                 if (e < n) atomicAdd(&sm.hist[(x[k] >> (8 * b)) & ((1u << h) - 1u)], 1u);
             }
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) transpose8(x[2 * b], x[2 * b + 1]);
         for (uint32_t k = 0; k < h; ++k) {
-            const uint32_t j = rb - 1u - k;
-            const uint32_t sel = (j & 3u) | ((j & 3u) + 4u) << 4;
-            const bool hi = j >= 4u;
+            const uint32_t jb8 = rb - 1u - k;
+            const uint32_t sel = (jb8 & 3u) | ((jb8 & 3u) + 4u) << 4;
+            const bool hi = jb8 >= 4u;
             const uint32_t t01 = __byte_perm(hi ? x[1] : x[0], hi ? x[3] : x[2], sel);
             const uint32_t t23 = __byte_perm(hi ? x[5] : x[4], hi ? x[7] : x[6], sel);
-            sm.plane[0][k][lane] = __byte_perm(t01, t23, 0x5410);
+            sm.plane[0][k][w0 + j] = __byte_perm(t01, t23, 0x5410);
         }
     }
     __syncwarp();
@@ -1177,7 +1052,8 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
     }
     if (matrix) {                                     // Z[c + l]: zeros of level l, any order
         for (uint32_t l = 0; l < h; ++l) {
-            uint32_t z = __popc(~sm.plane[0][l][lane]);
+            uint32_t z = 0;
+            for (uint32_t j = 0; j < KW; ++j) z += __popc(~sm.plane[0][l][w0 + j]);
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1) z += __shfl_xor_sync(kFull, z, d);
             if (lane == 0) t.zeros[rt.c + l] = z;
@@ -1187,8 +1063,8 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
 
     uint64_t *bv = t.bv;
     for (uint32_t l = 0; l < h; ++l) {
-        uint32_t(*cur)[33] = sm.plane[l & 1];
-        uint32_t(*nxt)[33] = sm.plane[(l + 1) & 1];
+        uint32_t(*cur)[NW + 1] = sm.plane[l & 1];
+        uint32_t(*nxt)[NW + 1] = sm.plane[(l + 1) & 1];
         const uint32_t base = 1u << l, s = h - l;
         // ---- class tables of level l (fold of the counts; starts in job order
         //      by reversed prefixes; interval starts in id (WT) / pi_l (WM) order)
@@ -1213,17 +1089,22 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
                 return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
             },
             [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[q] = v; });
-        const uint32_t m0 = cur[l][lane];
-        sm.lvl[lane] = m0;
-        if (lane < 4) sm.lvl[32 + lane] = 0;
-        const uint32_t z0 = __popc(~m0);
-        uint32_t inc = z0;
+        uint32_t mw[KW], zw[KW], zsum = 0;
+        for (uint32_t j = 0; j < KW; ++j) {
+            mw[j] = cur[l][w0 + j];
+            sm.lvl[w0 + j] = mw[j];
+            zw[j] = __popc(~mw[j]);
+            zsum += zw[j];
+        }
+        if (lane < 4) sm.lvl[NW + lane] = 0;
+        uint32_t inc = zsum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t y = __shfl_up_sync(kFull, inc, d);
             if (lane >= (uint32_t)d) inc += y;
         }
-        const uint32_t zt = __shfl_sync(kFull, inc, 31), zo = inc - z0;
+        const uint32_t zt = __shfl_sync(kFull, inc, 31);
+        uint32_t zo = inc - zsum;                     // zeros before word w0
         __syncwarp();
         // ---- copy every class's bits to its interval start in level c + l
         uint64_t *lv = bv + (uint64_t)(rt.c + l) * t.W;
@@ -1249,20 +1130,26 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
                 atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
             }
         }
-        // ---- stable split of every later plane by plane l
+        // ---- stable split of every later plane by plane l, word by word
         if (l + 1 < h) {
-            uint32_t mz[5], mo[5];
-            compress_moves(~m0, mz);
-            compress_moves(m0, mo);
-            for (uint32_t k = l + 1; k < h; ++k) {
-                const uint32_t x = cur[k][lane];
-                place_bits(nxt[k], zo, compress_apply(x, z0 == 32u ? ~0u : (1u << z0) - 1u, mz), z0);
-                place_bits(nxt[k], zt + 32u * lane - zo,
-                           compress_apply(x, z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u, mo), 32u - z0);
-                cur[k][lane] = 0;
+            for (uint32_t j = 0; j < KW; ++j) {
+                const uint32_t m0 = mw[j], z0 = zw[j];
+                uint32_t mz[5], mo[5];
+                compress_moves(~m0, mz);
+                compress_moves(m0, mo);
+                const uint32_t kz = z0 == 32u ? ~0u : (1u << z0) - 1u;
+                const uint32_t ko = z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u;
+                const uint32_t d1 = zt + 32u * (w0 + j) - zo;
+                for (uint32_t k = l + 1; k < h; ++k) {
+                    const uint32_t x = cur[k][w0 + j];
+                    place_bits(nxt[k], zo, compress_apply(x, kz, mz), z0);
+                    place_bits(nxt[k], d1, compress_apply(x, ko, mo), 32u - z0);
+                    cur[k][w0 + j] = 0;
+                }
+                zo += z0;
             }
             if (lane == 0)
-                for (uint32_t k = l + 1; k < h; ++k) cur[k][32] = 0;
+                for (uint32_t k = l + 1; k < h; ++k) cur[k][NW] = 0;
         }
         __syncwarp();
     }
@@ -1278,16 +1165,7 @@ cudaError_t configure_kernels()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_build_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_build<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BuildSmem<uint8_t>));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_build<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BuildSmem<uint16_t>));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_build<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(BuildSmem<uint32_t>));
+    return cudaFuncSetAttribute(k_build_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
 }
 
 cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s)
@@ -1317,22 +1195,11 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     k_blockscan<<<1, 256, 0, s>>>(a);
     k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
     if (prof) { profile_mark(2, false, s); profile_mark(0, true, s); }
-    if (a.any_plain) {
-        k_build_bs<<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    k_build_bs<<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    if (a.any_plain)
         k_build_small<<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
                         sizeof(SmallSmem) * kSmallWarps, s>>>(a);
-    }
-    if (!a.any_cut) {
-        if (prof) profile_mark(0, false, s, 2);
-        return cudaGetLastError();
-    }
-    if (smem_width == 1)
-        k_build<uint8_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint8_t>), s>>>(a);
-    else if (smem_width == 2)
-        k_build<uint16_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint16_t>), s>>>(a);
-    else
-        k_build<uint32_t><<<a.groups_ub, kThreads, sizeof(BuildSmem<uint32_t>), s>>>(a);
-    if (prof) profile_mark(0, false, s, a.any_plain ? 3 : 1);
+    if (prof) profile_mark(0, false, s, a.any_plain ? 2 : 1);
     return cudaGetLastError();
 }
 
