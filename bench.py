@@ -38,6 +38,27 @@ UNIT = "symbols/s"
 HBM_FALLBACK_GBS = 6800.0
 
 
+# DRAM bytes (read + write) per k_build_bs launch from the last ncu capture, keyed by
+# the SHA-256 of the kernel source it was taken on.  The capture ran n = 2^28 (256 MB,
+# above L2) and is scaled to the benchmark's n by symbol count; any later change to
+# the kernel source makes the figure stale, and `traffic` is then reported as null.
+TRAFFIC_CAPTURES = {}
+
+
+def kernel_source_hash():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1702_07578_gb300", "csrc", "wt_kernels.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def traffic_per_launch(n):
+    cap = TRAFFIC_CAPTURES.get(kernel_source_hash())
+    if cap is None:
+        return None
+    return cap["dram_bytes"] * n / cap["n"]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -272,7 +293,9 @@ def run_ours(args):
     # kernels per step: the library counts its launches per family; WM adds one Z-clear kernel
     launches = sum(v[1] for v in prof.values()) + args.steps
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": args.traffic, "kernel": "k_build_bs",
+                "frac": achieved / peak,
+                "traffic": args.traffic if args.traffic is not None else traffic_per_launch(n),
+                "kernel": "k_build_bs",
                 "peak_kind": peak_kind}
     step_frac = (2 * algo_bytes / (ms / 1e3) / 1e9) / peak
     breakdown = {f: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
