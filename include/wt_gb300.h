@@ -236,6 +236,35 @@ wt_status wt_server_get_stats(wt_server *s, wt_server_stats *st);
 /* Finish in-flight work, free everything. */
 void wt_server_destroy(wt_server *s);
 
+/* ---- queries: access / rank / select on built bit vectors ---------------------
+ * Queries on a built WT or WM (Sec. 2: "the bit vectors are augmented by binary
+ * rank and select structures" answer access, rank and select in O(lg sigma)).
+ *
+ * Rank support (caller-owned device memory of wt_rank_support_size bytes):
+ * for every level, the number of ones before each 256-bit block; for the WT,
+ * also every node's start and the ones before it, per level (levels < L).
+ * wt_rank_support_build fills it from d_bv (and, for the WM, d_zeros) on the
+ * stream.  n < 2^32.  The bit vectors must stay unchanged while queries run.
+ *
+ *   wt_access   d_out[k] = T[d_pos[k]]                      (d_pos[k] < n)
+ *   wt_rank     d_out[k] = number of d_sym[k] in T[0, d_pos[k])  (d_pos[k] <= n)
+ *   wt_select   d_out[k] = position of the d_j[k]-th (1-based) d_sym[k] in T,
+ *               or UINT64_MAX when there is no such occurrence
+ * Positions or symbols out of range give UINT64_MAX (rank, select) or
+ * 0xFFFFFFFF (access) in that slot.  All arrays are device memory; the calls
+ * are asynchronous on the stream. */
+wt_status wt_rank_support_size(wt_kind kind, uint64_t n, uint64_t sigma, size_t *bytes);
+wt_status wt_rank_support_build(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, uint64_t n,
+                                uint64_t sigma, void *d_rs, size_t rs_bytes, void *stream);
+wt_status wt_access(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, const void *d_rs, uint64_t n,
+                    uint64_t sigma, const uint64_t *d_pos, uint32_t count, uint32_t *d_out, void *stream);
+wt_status wt_rank(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, const void *d_rs, uint64_t n,
+                  uint64_t sigma, const uint32_t *d_sym, const uint64_t *d_pos, uint32_t count, uint64_t *d_out,
+                  void *stream);
+wt_status wt_select(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, const void *d_rs, uint64_t n,
+                    uint64_t sigma, const uint32_t *d_sym, const uint64_t *d_j, uint32_t count, uint64_t *d_out,
+                    void *stream);
+
 /* ---- diagnostics ----------------------------------------------------------
  * Per-kernel device time.  While enabled, every build records CUDA events on
  * its own stream before and after each kernel it launches (the work itself is

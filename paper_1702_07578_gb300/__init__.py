@@ -307,3 +307,46 @@ def wt_autotune_batched(kind, texts, sigmas, bvs, zeros=None, ws=None, stream=No
     _check(lib().wt_autotune_batched(kind, st, arr, len(texts), _ptr(ws), ws.numel(), _stream(stream),
                                      ctypes.byref(best)), "wt_autotune_batched")
     return best.value
+
+
+class WtIndex:
+    """access / rank / select on a built WT or WM (wt_rank_support_* and queries).
+
+    ``bv`` (and ``zeros`` for the WM) are the device tensors a build returned; they
+    must stay unchanged while the index is used.
+    """
+
+    def __init__(self, kind, bv, n, sigma, zeros=None, stream=None):
+        torch = _torch()
+        self.kind, self.bv, self.zeros, self.n, self.sigma = kind, bv, zeros, int(n), int(sigma)
+        size = ctypes.c_size_t(0)
+        _check(lib().wt_rank_support_size(kind, self.n, self.sigma, ctypes.byref(size)),
+               "wt_rank_support_size")
+        self.rs = torch.empty((max(size.value, 1),), dtype=torch.uint8, device=bv.device)
+        _check(lib().wt_rank_support_build(kind, _ptr(bv), _ptr(zeros), self.n, self.sigma,
+                                           _ptr(self.rs), self.rs.numel(), _stream(stream)),
+               "wt_rank_support_build")
+
+    def _common(self):
+        return (self.kind, _ptr(self.bv), _ptr(self.zeros), _ptr(self.rs), self.n, self.sigma)
+
+    def access(self, pos, stream=None):
+        torch = _torch()
+        out = torch.empty(pos.numel(), dtype=torch.int32, device=pos.device)
+        _check(lib().wt_access(*self._common(), _ptr(pos), pos.numel(), _ptr(out), _stream(stream)),
+               "wt_access")
+        return out
+
+    def rank(self, sym, pos, stream=None):
+        torch = _torch()
+        out = torch.empty(pos.numel(), dtype=torch.int64, device=pos.device)
+        _check(lib().wt_rank(*self._common(), _ptr(sym), _ptr(pos), pos.numel(), _ptr(out),
+                             _stream(stream)), "wt_rank")
+        return out
+
+    def select(self, sym, j, stream=None):
+        torch = _torch()
+        out = torch.empty(j.numel(), dtype=torch.int64, device=j.device)
+        _check(lib().wt_select(*self._common(), _ptr(sym), _ptr(j), j.numel(), _ptr(out),
+                               _stream(stream)), "wt_select")
+        return out

@@ -154,6 +154,15 @@ SIGNATURES = {
     "wt_autotune_batched": (_C.c_int, [_C.c_int, _C.c_int, _C.POINTER(WtTextDesc), _C.c_uint32,
                                        _C.c_void_p, _C.c_size_t, _C.c_void_p,
                                        _C.POINTER(_C.c_uint32)]),
+    "wt_rank_support_size": (_C.c_int, [_C.c_int, _C.c_uint64, _C.c_uint64, _C.POINTER(_C.c_size_t)]),
+    "wt_rank_support_build": (_C.c_int, [_C.c_int, _C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64,
+                                         _C.c_void_p, _C.c_size_t, _C.c_void_p]),
+    "wt_access": (_C.c_int, [_C.c_int, _C.c_void_p, _C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64,
+                             _C.c_void_p, _C.c_uint32, _C.c_void_p, _C.c_void_p]),
+    "wt_rank": (_C.c_int, [_C.c_int, _C.c_void_p, _C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64,
+                           _C.c_void_p, _C.c_void_p, _C.c_uint32, _C.c_void_p, _C.c_void_p]),
+    "wt_select": (_C.c_int, [_C.c_int, _C.c_void_p, _C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64,
+                             _C.c_void_p, _C.c_void_p, _C.c_uint32, _C.c_void_p, _C.c_void_p]),
     "wt_profile_enable": (None, [_C.c_int]),
     "wt_profile_read": (_C.c_int, [_C.POINTER(WtProfile), _C.c_int]),
 }

@@ -1,0 +1,460 @@
+// access / rank / select on built wavelet trees and matrices (see the "queries"
+// section of include/wt_gb300.h).  The bit vectors of every level get a rank
+// directory: the number of ones before each 256-bit block.  The wavelet tree also
+// gets, per level, every node's start and the ones before it, so that a query
+// follows a root-to-leaf (or leaf-to-root) path with one rank or select per level
+// (Sec. 2 for the tree, Sec. 5 for the matrix navigation: position i of level l
+// moves to rank0(i), or to Z[l] + rank1(i)).
+#include <cstdint>
+
+#include "wt_internal.h"
+
+namespace wtg {
+namespace {
+
+constexpr uint32_t kDirChunk = 4096;       // directory entries per scan chunk
+constexpr uint64_t kNone = ~0ull;
+
+struct RsLayout {
+    uint32_t L = 0;
+    uint64_t W = 0, NB = 0, nchunks = 0;
+    size_t off_dir = 0, off_csum = 0, off_S = 0, off_R = 0, bytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+uint32_t lvls(uint64_t sigma)
+{
+    uint32_t L = 0;
+    while (L < 64 && (1ull << L) < sigma) ++L;
+    return L;
+}
+
+wt_status layout(wt_kind kind, uint64_t n, uint64_t sigma, RsLayout &r)
+{
+    if (kind != WT_TREE && kind != WT_MATRIX) return WT_ERR_INVALID_ARG;
+    if (sigma == 0 || sigma > (1ull << 32) || n >= (1ull << 32)) return WT_ERR_INVALID_ARG;
+    r.L = lvls(sigma);
+    if (kind == WT_TREE && r.L > (uint32_t)kMaxTreeSigmaLog) return WT_ERR_INVALID_ARG;
+    r.W = (n + 63) / 64;
+    r.NB = (r.W + 3) / 4 + 1;                               // last entry: total ones
+    r.nchunks = (r.NB + kDirChunk - 1) / kDirChunk;
+    size_t off = 0;
+    r.off_dir = off;
+    off = align256(off + sizeof(uint32_t) * r.L * r.NB);
+    r.off_csum = off;
+    off = align256(off + sizeof(uint32_t) * r.L * r.nchunks);
+    const size_t tbl = kind == WT_TREE && r.L > 0 ? (size_t)((1ull << r.L) - 1 + r.L) : 0;
+    r.off_S = off;
+    off = align256(off + sizeof(uint32_t) * tbl);
+    r.off_R = off;
+    off = align256(off + sizeof(uint32_t) * tbl);
+    r.bytes = off > 0 ? off : 256;
+    return WT_OK;
+}
+
+struct QArgs {
+    const uint64_t *bv;       // L * W words
+    const uint64_t *zeros;    // WM
+    const uint32_t *dir;      // L * NB
+    uint32_t *dirw;           // same, writable (build)
+    uint32_t *csum;           // L * nchunks
+    uint32_t *S, *R;          // WT node starts / ones before them, level l at (2^l - 1 + l)
+    uint64_t n, W, NB, nchunks;
+    uint32_t L;
+    uint32_t kind;
+};
+
+__device__ __forceinline__ size_t tbl_off(uint32_t l) { return ((size_t)1 << l) - 1 + l; }
+
+// ones in bits [0, i) of level l
+__device__ __forceinline__ uint32_t rank1(const QArgs &a, uint32_t l, uint64_t i)
+{
+    const uint64_t *bv = a.bv + (uint64_t)l * a.W;
+    const uint64_t b = i >> 8, w = i >> 6;
+    uint32_t r = a.dir[(uint64_t)l * a.NB + b];
+    for (uint64_t k = b * 4; k < w; ++k) r += __popcll(bv[k]);
+    if (i & 63) r += __popcll(bv[w] & ((1ull << (i & 63)) - 1ull));
+    return r;
+}
+
+// position of the t-th (0-based) set bit of x
+__device__ __forceinline__ uint32_t select_in_word(uint64_t x, uint32_t t)
+{
+    uint32_t pos = 0, v = (uint32_t)x, c = __popc(v);
+    if (t >= c) {
+        t -= c;
+        v = (uint32_t)(x >> 32);
+        pos = 32;
+    }
+    c = __popc(v & 0xffffu);
+    if (t >= c) { t -= c; v >>= 16; pos += 16; }
+    c = __popc(v & 0xffu);
+    if (t >= c) { t -= c; v >>= 8; pos += 8; }
+    c = __popc(v & 0xfu);
+    if (t >= c) { t -= c; v >>= 4; pos += 4; }
+    c = __popc(v & 0x3u);
+    if (t >= c) { t -= c; v >>= 2; pos += 2; }
+    if (t >= (v & 1u)) pos += 1;
+    return pos;
+}
+
+// position of the j-th (0-based) bit equal to `one` in level l (j must exist)
+__device__ __forceinline__ uint64_t select_bit(const QArgs &a, uint32_t l, uint64_t j, bool one)
+{
+    const uint64_t *bv = a.bv + (uint64_t)l * a.W;
+    const uint32_t *dir = a.dir + (uint64_t)l * a.NB;
+    uint64_t lo = 0, hi = a.NB - 1;                         // last block with count-before <= j
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint64_t before = one ? dir[mid] : mid * 256 - dir[mid];
+        if (before <= j) lo = mid; else hi = mid;
+    }
+    uint64_t rem = j - (one ? dir[lo] : lo * 256 - dir[lo]);
+    for (uint64_t k = lo * 4;; ++k) {
+        const uint64_t x = one ? bv[k] : ~bv[k];
+        const uint32_t c = __popcll(x);
+        if (rem < c) return k * 64 + select_in_word(x, (uint32_t)rem);
+        rem -= c;
+    }
+}
+
+// ---- directory: counts of every 256-bit block, scanned per level ------------
+
+__device__ __forceinline__ uint32_t block_ones(const QArgs &a, uint32_t l, uint64_t b)
+{
+    const uint64_t *bv = a.bv + (uint64_t)l * a.W;
+    uint32_t c = 0;
+    for (uint64_t k = b * 4; k < b * 4 + 4 && k < a.W; ++k) c += __popcll(bv[k]);
+    return c;
+}
+
+__device__ __forceinline__ uint32_t block_scan_1024(uint32_t v, uint32_t *ws, uint32_t *total)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= (uint32_t)d) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    const uint32_t x = ws[lane];
+    uint32_t p = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, p, d);
+        if (lane >= (uint32_t)d) p += y;
+    }
+    *total = __shfl_sync(0xffffffffu, p, 31);
+    const uint32_t before = __shfl_sync(0xffffffffu, p - x, warp);
+    __syncthreads();
+    return before + inc - v;
+}
+
+// grid (nchunks, L), 1024 threads: ones of each chunk of 4096 blocks
+__global__ void __launch_bounds__(1024) k_dir_chunks(QArgs a)
+{
+    __shared__ uint32_t ws[32];
+    const uint32_t l = blockIdx.y;
+    const uint64_t b0 = (uint64_t)blockIdx.x * kDirChunk;
+    uint32_t s = 0;
+    for (uint32_t j = 0; j < 4; ++j) {
+        const uint64_t b = b0 + threadIdx.x * 4 + j;
+        if (b + 1 < a.NB) s += block_ones(a, l, b);
+    }
+    uint32_t total;
+    block_scan_1024(s, ws, &total);
+    if (threadIdx.x == 0) a.csum[(uint64_t)l * a.nchunks + blockIdx.x] = total;
+}
+
+// grid (L), 1024 threads: exclusive scan of the chunk sums of a level
+__global__ void __launch_bounds__(1024) k_dir_chunk_scan(QArgs a)
+{
+    __shared__ uint32_t ws[32];
+    uint32_t *c = a.csum + (uint64_t)blockIdx.x * a.nchunks;
+    uint32_t carry = 0;
+    for (uint64_t c0 = 0; c0 < a.nchunks; c0 += 1024) {
+        const uint64_t i = c0 + threadIdx.x;
+        const uint32_t v = i < a.nchunks ? c[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_scan_1024(v, ws, &total);
+        if (i < a.nchunks) c[i] = carry + ex;
+        carry += total;
+    }
+}
+
+// grid (nchunks, L), 1024 threads: exclusive prefix of every block
+__global__ void __launch_bounds__(1024) k_dir_apply(QArgs a)
+{
+    __shared__ uint32_t ws[32];
+    const uint32_t l = blockIdx.y;
+    const uint64_t b0 = (uint64_t)blockIdx.x * kDirChunk;
+    uint32_t c[4], s = 0;
+    for (uint32_t j = 0; j < 4; ++j) {
+        const uint64_t b = b0 + threadIdx.x * 4 + j;
+        c[j] = b + 1 < a.NB ? block_ones(a, l, b) : 0u;
+        s += c[j];
+    }
+    uint32_t total;
+    uint32_t run = a.csum[(uint64_t)l * a.nchunks + blockIdx.x] + block_scan_1024(s, ws, &total);
+    for (uint32_t j = 0; j < 4; ++j) {
+        const uint64_t b = b0 + threadIdx.x * 4 + j;
+        if (b < a.NB) a.dirw[(uint64_t)l * a.NB + b] = run;
+        run += c[j];
+    }
+}
+
+// WT node tables, level l: node p covers [S[p], S[p+1]); R[p] = ones before S[p]
+__global__ void k_tree_nodes(QArgs a, uint32_t l)
+{
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nodes = 1ull << l;
+    if (l == 0 && p == 0) {
+        a.S[tbl_off(0)] = 0;
+        a.S[tbl_off(0) + 1] = (uint32_t)a.n;
+    }
+    if (p > nodes) return;
+    const uint32_t *S = a.S + tbl_off(l);
+    uint32_t *R = a.R + tbl_off(l);
+    if (p == nodes) {                                         // end of the level
+        R[p] = rank1(a, l, a.n);
+        if (l + 1 < a.L) a.S[tbl_off(l + 1) + 2 * nodes] = (uint32_t)a.n;
+        return;
+    }
+    const uint32_t s = l == 0 ? 0u : S[p], e = l == 0 ? (uint32_t)a.n : S[p + 1];
+    const uint32_t rs = rank1(a, l, s);
+    R[p] = rs;
+    if (l + 1 < a.L) {
+        const uint32_t ones = rank1(a, l, e) - rs;
+        const uint32_t z = (e - s) - ones;
+        a.S[tbl_off(l + 1) + 2 * p] = s;
+        a.S[tbl_off(l + 1) + 2 * p + 1] = s + z;
+    }
+}
+
+}  // namespace
+}  // namespace wtg
+
+// ---- queries: one thread per query ------------------------------------------
+
+namespace wtg {
+namespace {
+
+__device__ __forceinline__ uint32_t cbit(uint32_t c, uint32_t l, uint32_t L) { return (c >> (L - 1u - l)) & 1u; }
+
+// number of c in T[0, i)
+__device__ uint64_t rank_sym(const QArgs &a, uint32_t c, uint64_t i)
+{
+    if (a.kind == WT_TREE) {
+        uint64_t k = i, p = 0;
+        for (uint32_t l = 0; l < a.L; ++l) {
+            const uint32_t s = a.S[tbl_off(l) + p];
+            const uint64_t ones = rank1(a, l, s + k) - a.R[tbl_off(l) + p];
+            const uint32_t b = cbit(c, l, a.L);
+            k = b ? ones : k - ones;
+            p = 2 * p + b;
+        }
+        return k;
+    }
+    uint64_t s = 0, e = i;
+    for (uint32_t l = 0; l < a.L; ++l) {
+        const uint64_t rs = rank1(a, l, s), re = rank1(a, l, e);
+        if (cbit(c, l, a.L)) {
+            s = a.zeros[l] + rs;
+            e = a.zeros[l] + re;
+        } else {
+            s -= rs;
+            e -= re;
+        }
+    }
+    return e - s;
+}
+
+__global__ void k_access(QArgs a, const uint64_t *pos, uint32_t count, uint32_t *out)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    uint64_t i = pos[k];
+    if (i >= a.n) { out[k] = 0xffffffffu; return; }
+    uint32_t sym = 0;
+    if (a.kind == WT_TREE) {
+        uint64_t p = 0;
+        for (uint32_t l = 0; l < a.L; ++l) {
+            const uint64_t *bv = a.bv + (uint64_t)l * a.W;
+            const uint32_t b = (uint32_t)(bv[i >> 6] >> (i & 63)) & 1u;
+            const uint32_t s = a.S[tbl_off(l) + p];
+            const uint64_t ones = rank1(a, l, i) - a.R[tbl_off(l) + p];
+            sym = (sym << 1) | b;
+            if (l + 1 < a.L) {
+                p = 2 * p + b;
+                i = a.S[tbl_off(l + 1) + p] + (b ? ones : (i - s) - ones);
+            }
+        }
+    } else {
+        for (uint32_t l = 0; l < a.L; ++l) {
+            const uint64_t *bv = a.bv + (uint64_t)l * a.W;
+            const uint32_t b = (uint32_t)(bv[i >> 6] >> (i & 63)) & 1u;
+            const uint64_t r1 = rank1(a, l, i);
+            sym = (sym << 1) | b;
+            i = b ? a.zeros[l] + r1 : i - r1;
+        }
+    }
+    out[k] = sym;
+}
+
+__global__ void k_rank(QArgs a, const uint32_t *sym, const uint64_t *pos, uint32_t count, uint64_t *out)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const uint32_t c = sym[k];
+    const uint64_t i = pos[k];
+    if (i > a.n || (a.L < 32 && (c >> a.L) != 0)) { out[k] = kNone; return; }
+    out[k] = rank_sym(a, c, i);
+}
+
+__global__ void k_select(QArgs a, const uint32_t *sym, const uint64_t *jj, uint32_t count, uint64_t *out)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const uint32_t c = sym[k];
+    const uint64_t j = jj[k];
+    if (j == 0 || (a.L < 32 && (c >> a.L) != 0)) { out[k] = kNone; return; }
+    if (j > rank_sym(a, c, a.n)) { out[k] = kNone; return; }
+    uint64_t pos = j - 1;
+    if (a.kind == WT_TREE) {
+        for (uint32_t l = a.L; l-- > 0;) {                     // from the leaf up
+            const uint64_t p = (uint64_t)c >> (a.L - l);       // node of c at level l
+            const uint32_t b = cbit(c, l, a.L);
+            const uint32_t s = a.S[tbl_off(l) + p], r = a.R[tbl_off(l) + p];
+            const uint64_t before = b ? r : s - r;             // b-bits before the node
+            pos = select_bit(a, l, before + pos, b != 0) - s;
+        }
+    } else {
+        uint64_t s = 0;                                        // start of c's interval below the last level
+        for (uint32_t l = 0; l < a.L; ++l) {
+            const uint64_t rs = rank1(a, l, s);
+            s = cbit(c, l, a.L) ? a.zeros[l] + rs : s - rs;
+        }
+        pos += s;
+        for (uint32_t l = a.L; l-- > 0;) {
+            if (cbit(c, l, a.L)) pos = select_bit(a, l, pos - a.zeros[l], true);
+            else pos = select_bit(a, l, pos, false);
+        }
+    }
+    out[k] = pos;
+}
+
+QArgs make_args(const RsLayout &r, wt_kind kind, const uint64_t *bv, const uint64_t *zeros, const void *rs,
+                uint64_t n)
+{
+    QArgs a{};
+    uint8_t *base = const_cast<uint8_t *>(static_cast<const uint8_t *>(rs));
+    a.bv = bv;
+    a.zeros = zeros;
+    a.dir = reinterpret_cast<const uint32_t *>(base + r.off_dir);
+    a.dirw = reinterpret_cast<uint32_t *>(base + r.off_dir);
+    a.csum = reinterpret_cast<uint32_t *>(base + r.off_csum);
+    a.S = reinterpret_cast<uint32_t *>(base + r.off_S);
+    a.R = reinterpret_cast<uint32_t *>(base + r.off_R);
+    a.n = n;
+    a.W = r.W;
+    a.NB = r.NB;
+    a.nchunks = r.nchunks;
+    a.L = r.L;
+    a.kind = (uint32_t)kind;
+    return a;
+}
+
+wt_status check_query(wt_kind kind, const uint64_t *bv, const uint64_t *zeros, const void *rs, uint64_t n,
+                      uint64_t sigma, RsLayout &r)
+{
+    wt_status st = layout(kind, n, sigma, r);
+    if (st != WT_OK) return st;
+    if (rs == nullptr) return WT_ERR_INVALID_ARG;
+    if (r.L > 0 && n > 0 && bv == nullptr) return WT_ERR_INVALID_ARG;
+    if (kind == WT_MATRIX && r.L > 0 && zeros == nullptr) return WT_ERR_INVALID_ARG;
+    return WT_OK;
+}
+
+}  // namespace
+}  // namespace wtg
+
+using namespace wtg;
+
+extern "C" {
+
+wt_status wt_rank_support_size(wt_kind kind, uint64_t n, uint64_t sigma, size_t *bytes)
+{
+    if (bytes == nullptr) return WT_ERR_INVALID_ARG;
+    RsLayout r;
+    wt_status st = layout(kind, n, sigma, r);
+    if (st == WT_OK) *bytes = r.bytes;
+    return st;
+}
+
+wt_status wt_rank_support_build(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, uint64_t n,
+                                uint64_t sigma, void *d_rs, size_t rs_bytes, void *stream)
+{
+    RsLayout r;
+    wt_status st = check_query(kind, d_bv, d_zeros, d_rs, n, sigma, r);
+    if (st != WT_OK) return st;
+    if (rs_bytes < r.bytes) return WT_ERR_OUT_OF_MEMORY;
+    if (r.L == 0) return WT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    QArgs a = make_args(r, kind, d_bv, d_zeros, d_rs, n);
+    const dim3 grid((uint32_t)r.nchunks, r.L);
+    k_dir_chunks<<<grid, 1024, 0, s>>>(a);
+    k_dir_chunk_scan<<<r.L, 1024, 0, s>>>(a);
+    k_dir_apply<<<grid, 1024, 0, s>>>(a);
+    if (kind == WT_TREE)
+        for (uint32_t l = 0; l < r.L; ++l) {
+            const uint64_t threads = (1ull << l) + 1;
+            k_tree_nodes<<<(uint32_t)((threads + 255) / 256), 256, 0, s>>>(a, l);
+        }
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+wt_status wt_access(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, const void *d_rs, uint64_t n,
+                    uint64_t sigma, const uint64_t *d_pos, uint32_t count, uint32_t *d_out, void *stream)
+{
+    RsLayout r;
+    wt_status st = check_query(kind, d_bv, d_zeros, d_rs, n, sigma, r);
+    if (st != WT_OK) return st;
+    if (count == 0) return WT_OK;
+    if (d_pos == nullptr || d_out == nullptr) return WT_ERR_INVALID_ARG;
+    QArgs a = make_args(r, kind, d_bv, d_zeros, d_rs, n);
+    k_access<<<(count + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(a, d_pos, count, d_out);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+wt_status wt_rank(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, const void *d_rs, uint64_t n,
+                  uint64_t sigma, const uint32_t *d_sym, const uint64_t *d_pos, uint32_t count, uint64_t *d_out,
+                  void *stream)
+{
+    RsLayout r;
+    wt_status st = check_query(kind, d_bv, d_zeros, d_rs, n, sigma, r);
+    if (st != WT_OK) return st;
+    if (count == 0) return WT_OK;
+    if (d_sym == nullptr || d_pos == nullptr || d_out == nullptr) return WT_ERR_INVALID_ARG;
+    QArgs a = make_args(r, kind, d_bv, d_zeros, d_rs, n);
+    k_rank<<<(count + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(a, d_sym, d_pos, count, d_out);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+wt_status wt_select(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros, const void *d_rs, uint64_t n,
+                    uint64_t sigma, const uint32_t *d_sym, const uint64_t *d_j, uint32_t count, uint64_t *d_out,
+                    void *stream)
+{
+    RsLayout r;
+    wt_status st = check_query(kind, d_bv, d_zeros, d_rs, n, sigma, r);
+    if (st != WT_OK) return st;
+    if (count == 0) return WT_OK;
+    if (d_sym == nullptr || d_j == nullptr || d_out == nullptr) return WT_ERR_INVALID_ARG;
+    QArgs a = make_args(r, kind, d_bv, d_zeros, d_rs, n);
+    k_select<<<(count + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(a, d_sym, d_j, count, d_out);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+}  // extern "C"
