@@ -525,6 +525,68 @@ def run_served(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# queries: access / rank / select on the built 2^30-symbol WT and WM
+
+def run_queries(args):
+    import torch
+    import paper_1702_07578_gb300 as wtg
+
+    rank, local, world, pg = dist()
+    torch.cuda.set_device(local)
+    T, sigma, desc = load_workload("bytes", args.n_log2)
+    n = T.size
+    text = torch.from_numpy(T).cuda()
+    q = args.queries
+    g = torch.Generator(device="cuda").manual_seed(7)
+    pos = torch.randint(0, n, (q,), device="cuda", generator=g, dtype=torch.int64)
+    sym = text[torch.randint(0, n, (q,), device="cuda", generator=g)].to(torch.int32)
+    jj = torch.randint(1, 1 << 16, (q,), device="cuda", generator=g, dtype=torch.int64)
+    res = {}
+    for name, kind in (("wt", wtg.WT_TREE), ("wm", wtg.WT_MATRIX)):
+        if kind == wtg.WT_TREE:
+            bv, z = wtg.wt_build(text, sigma), None
+        else:
+            bv, z = wtg.wm_build(text, sigma)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        idx = wtg.WtIndex(kind, bv, n, sigma, z)
+        e1.record()
+        torch.cuda.synchronize()
+        res[f"{name}_rank_support_ms"] = e0.elapsed_time(e1)
+        for op in ("access", "rank", "select"):
+            def call():
+                if op == "access":
+                    return idx.access(pos)
+                if op == "rank":
+                    return idx.rank(sym, pos)
+                return idx.select(sym, jj)
+            call()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.steps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            res[f"{name}_{op}_per_s"] = q * args.steps / (e0.elapsed_time(e1) / 1e3)
+        del idx, bv, z
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "queries/s on a built WT and WM (access, rank, select), n = 2^30 uint8, sigma = 256",
+        "value": res["wm_access_per_s"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": desc, "queries_per_launch": q,
+                   "positions": "uniform random", "symbols": "drawn from the text",
+                   "select_j": "uniform in [1, 2^16)"},
+        "results": res,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -532,7 +594,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bytes",
-                    choices=["bytes", "small", "large_alphabet", "batched", "served"])
+                    choices=["bytes", "small", "large_alphabet", "batched", "served", "queries"])
+    ap.add_argument("--queries", type=int, default=1 << 24)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=400.0, help="served: arrivals per second")
@@ -551,6 +614,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "queries":
+        return run_queries(args)
     return run_ours(args)
 
 
