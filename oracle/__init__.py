@@ -14,6 +14,7 @@ uint64, level-major, bit j of a level at bit ``j & 63`` of word ``j >> 6``):
 ``wm(T, sigma)``            WM and Z from the definition (Sec. 5)
 ``pc(kind, T, sigma)``      Algorithm 1, pcWT / pcWM (Sec. 3.1, Sec. 5.1)
 ``ps(kind, T, sigma, p)``   Algorithm 2, psWT / psWM with p slices (Sec. 3.2.1)
+``wt2wm(T, sigma, l, i)``   Lemma 3: WT position -> WM position (``lemma3.py``, numpy)
 """
 from __future__ import annotations
 
@@ -142,3 +143,6 @@ def bits_string(bv_level, n):
     for j in range(n):
         out.append("1" if (int(bv_level[j >> 6]) >> (j & 63)) & 1 else "0")
     return "".join(out)
+
+
+from .lemma3 import wt2wm, wt2wm_tables  # noqa: E402,F401
