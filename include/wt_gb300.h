@@ -265,6 +265,37 @@ wt_status wt_select(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros,
                     uint64_t sigma, const uint32_t *d_sym, const uint64_t *d_j, uint32_t count, uint64_t *d_out,
                     void *stream);
 
+/* ---- WT position -> WM position (Sec. 5.2, Lemma 3) --------------------------
+ * For a text whose WT and WM are both built: position i of WT level l and
+ * position j of WM level l hold the bit of the same text symbol, with
+ *   j = i                                  for l <= 1,
+ *   j = X[2^l - 2 + bp] + off              otherwise,
+ * bp = prefix(l, rank0(U, select1(U, i+1))) and
+ * off = i - rank1(U, select0(U, bp << (L - l))).
+ * U is the unary histogram 1^h(0) 0 1^h(1) 0 ... of the 2^L characters (n + 2^L
+ * bits, with its own rank directory); X holds the WM interval starts of levels
+ * 1 .. L-1, level l at X[2^l - 2, 2^(l+1) - 2).  (The lemma's statement writes
+ * X[2^(l-1) - 2 + bp]; that form lets levels overlap, and the proof's index is
+ * the one used here.)
+ *
+ * wt_wt2wm_size    bytes of the map for (n, sigma); sigma <= 2^24 as for the WT
+ *                  rank support.
+ * wt_wt2wm_build   fills d_map (caller-owned device memory, map_bytes >= size)
+ *                  from the WT bit vectors d_bv and their rank support d_rs
+ *                  (wt_rank_support_build with kind WT_TREE, same n and sigma);
+ *                  the histogram is read off the node tables of level L-1.
+ *                  Asynchronous on the stream; d_bv and d_rs must stay unchanged
+ *                  until it has run.  WT_ERR_OUT_OF_MEMORY if map_bytes is short.
+ * wt_wt2wm         d_out[k] = j for (d_level[k], d_pos[k]); UINT64_MAX where
+ *                  d_level[k] >= L or d_pos[k] >= n.  Device arrays, asynchronous.
+ * Select on U is a binary search over its rank directory plus a scan of one
+ * 256-bit block (O(lg n)), not the constant-time select the lemma assumes. */
+wt_status wt_wt2wm_size(uint64_t n, uint64_t sigma, size_t *bytes);
+wt_status wt_wt2wm_build(const uint64_t *d_bv, const void *d_rs, uint64_t n, uint64_t sigma, void *d_map,
+                         size_t map_bytes, void *stream);
+wt_status wt_wt2wm(const void *d_map, uint64_t n, uint64_t sigma, const uint32_t *d_level, const uint64_t *d_pos,
+                   uint32_t count, uint64_t *d_out, void *stream);
+
 /* ---- diagnostics ----------------------------------------------------------
  * Per-kernel device time.  While enabled, every build records CUDA events on
  * its own stream before and after each kernel it launches (the work itself is

@@ -350,3 +350,31 @@ class WtIndex:
         _check(lib().wt_select(*self._common(), _ptr(sym), _ptr(j), j.numel(), _ptr(out),
                                _stream(stream)), "wt_select")
         return out
+
+
+class WtToWmMap:
+    """Lemma 3: position i of WT level l -> position j of WM level l (wt_wt2wm_*).
+
+    Built from a WT's ``WtIndex`` (its bit vectors and rank support, which must
+    stay unchanged while the map is built).
+    """
+
+    def __init__(self, index, stream=None):
+        torch = _torch()
+        if index.kind != WT_TREE:
+            raise ValueError("WtToWmMap needs the rank support of a wavelet tree")
+        self.n, self.sigma = index.n, index.sigma
+        size = ctypes.c_size_t(0)
+        _check(lib().wt_wt2wm_size(self.n, self.sigma, ctypes.byref(size)), "wt_wt2wm_size")
+        self.map = torch.empty((max(size.value, 1),), dtype=torch.uint8, device=index.bv.device)
+        _check(lib().wt_wt2wm_build(_ptr(index.bv), _ptr(index.rs), self.n, self.sigma, _ptr(self.map),
+                                    self.map.numel(), _stream(stream)), "wt_wt2wm_build")
+
+    def __call__(self, level, pos, stream=None):
+        torch = _torch()
+        if level.numel() != pos.numel():
+            raise ValueError("level and pos must have the same length")
+        out = torch.empty(pos.numel(), dtype=torch.int64, device=pos.device)
+        _check(lib().wt_wt2wm(_ptr(self.map), self.n, self.sigma, _ptr(level), _ptr(pos), pos.numel(),
+                              _ptr(out), _stream(stream)), "wt_wt2wm")
+        return out

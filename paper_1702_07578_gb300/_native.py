@@ -163,6 +163,11 @@ SIGNATURES = {
                            _C.c_void_p, _C.c_void_p, _C.c_uint32, _C.c_void_p, _C.c_void_p]),
     "wt_select": (_C.c_int, [_C.c_int, _C.c_void_p, _C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64,
                              _C.c_void_p, _C.c_void_p, _C.c_uint32, _C.c_void_p, _C.c_void_p]),
+    "wt_wt2wm_size": (_C.c_int, [_C.c_uint64, _C.c_uint64, _C.POINTER(_C.c_size_t)]),
+    "wt_wt2wm_build": (_C.c_int, [_C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64, _C.c_void_p,
+                                  _C.c_size_t, _C.c_void_p]),
+    "wt_wt2wm": (_C.c_int, [_C.c_void_p, _C.c_uint64, _C.c_uint64, _C.c_void_p, _C.c_void_p, _C.c_uint32,
+                            _C.c_void_p, _C.c_void_p]),
     "wt_profile_enable": (None, [_C.c_int]),
     "wt_profile_read": (_C.c_int, [_C.POINTER(WtProfile), _C.c_int]),
 }

@@ -458,3 +458,180 @@ wt_status wt_select(wt_kind kind, const uint64_t *d_bv, const uint64_t *d_zeros,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Lemma 3: WT position -> WM position.  U = 1^Hist[0] 0 1^Hist[1] 0 ... (one run
+// of ones per character of [0, 2^L), each followed by a zero) with rank/select,
+// and X = the WM interval starts of levels 1 .. L-1, level l at X[2^l - 2 + p]
+// (the proof's indexing; the statement's 2^(l-1) - 2 disagrees with the stated
+// storage range X[2^l - 2, 2^(l+1))).  The histogram is read off the WT's node
+// tables: node p of level L-1 holds characters 2p and 2p+1.
+
+namespace wtg {
+namespace {
+
+struct MapLayout {
+    RsLayout wt;                  // the WT rank support this map is built from
+    uint32_t L = 0;
+    uint64_t ubits = 0, uW = 0, uNB = 0, unchunks = 0;
+    size_t off_u = 0, off_udir = 0, off_ucsum = 0, off_x = 0, bytes = 0;
+};
+
+wt_status map_layout(uint64_t n, uint64_t sigma, MapLayout &m)
+{
+    wt_status st = layout(WT_TREE, n, sigma, m.wt);
+    if (st != WT_OK) return st;
+    m.L = m.wt.L;
+    m.ubits = n + (1ull << m.L);
+    m.uW = (m.ubits + 63) / 64;
+    m.uNB = (m.uW + 3) / 4 + 1;
+    m.unchunks = (m.uNB + kDirChunk - 1) / kDirChunk;
+    size_t off = 0;
+    m.off_u = off;
+    off = align256(off + 8 * m.uW);
+    m.off_udir = off;
+    off = align256(off + 4 * m.uNB);
+    m.off_ucsum = off;
+    off = align256(off + 4 * m.unchunks);
+    m.off_x = off;
+    off = align256(off + 4 * (m.L >= 1 ? (1ull << m.L) : 1ull));
+    m.bytes = off;
+    return WT_OK;
+}
+
+QArgs u_args(const MapLayout &m, void *d_map)
+{
+    uint8_t *b = static_cast<uint8_t *>(d_map);
+    QArgs a{};
+    a.bv = reinterpret_cast<const uint64_t *>(b + m.off_u);
+    a.dir = reinterpret_cast<const uint32_t *>(b + m.off_udir);
+    a.dirw = reinterpret_cast<uint32_t *>(b + m.off_udir);
+    a.csum = reinterpret_cast<uint32_t *>(b + m.off_ucsum);
+    a.n = m.ubits;
+    a.W = m.uW;
+    a.NB = m.uNB;
+    a.nchunks = m.unchunks;
+    a.L = 1;
+    return a;
+}
+
+// U: ones everywhere below ubits, zeros above
+__global__ void k_u_fill(uint64_t *u, uint64_t uW, uint64_t ubits)
+{
+    const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= uW) return;
+    const uint64_t lo = w * 64;
+    u[w] = lo + 64 <= ubits ? ~0ull : (ubits > lo ? (1ull << (ubits - lo)) - 1ull : 0ull);
+}
+
+// the zero after character c's run: position (characters <= c) + c
+__global__ void k_u_zeros(QArgs wt, uint64_t *u)
+{
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;   // node of level L-1
+    const uint32_t l = wt.L - 1;
+    if (p >= (1ull << l)) return;
+    const uint32_t s = wt.S[tbl_off(l) + p], e = wt.S[tbl_off(l) + p + 1];
+    const uint32_t ones = wt.R[tbl_off(l) + p + 1] - wt.R[tbl_off(l) + p];
+    const uint64_t c0 = 2 * p, c1 = 2 * p + 1;
+    const uint64_t end0 = (uint64_t)s + ((e - s) - ones);               // characters <= c0
+    const uint64_t end1 = e;                                            // characters <= c1
+    const uint64_t z0 = end0 + c0, z1 = end1 + c1;
+    atomicAnd(reinterpret_cast<unsigned long long *>(u + (z0 >> 6)), ~(1ull << (z0 & 63)));
+    atomicAnd(reinterpret_cast<unsigned long long *>(u + (z1 >> 6)), ~(1ull << (z1 & 63)));
+}
+
+// X for level l (one block): exclusive scan of the level's interval sizes in
+// bit-reversal order (Sec. 5.1); sizes from the WT node starts.
+__global__ void __launch_bounds__(1024) k_x_level(QArgs wt, uint32_t *X, uint32_t l)
+{
+    __shared__ uint32_t ws[32];
+    const uint64_t cnt = 1ull << l;
+    const uint32_t *S = wt.S + tbl_off(l);
+    uint32_t carry = 0;
+    for (uint64_t r0 = 0; r0 < cnt; r0 += 1024) {
+        const uint64_t r = r0 + threadIdx.x;
+        uint32_t sz = 0, p = 0;
+        if (r < cnt) {
+            p = __brev((uint32_t)r) >> (32 - l);
+            sz = S[p + 1] - S[p];
+        }
+        uint32_t total;
+        const uint32_t ex = block_scan_1024(sz, ws, &total);
+        if (r < cnt) X[cnt - 2 + p] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void k_wt2wm(QArgs u, const uint32_t *X, uint32_t L, uint64_t n, const uint32_t *lvl, const uint64_t *pos,
+                        uint32_t count, uint64_t *out)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const uint32_t l = lvl[k];
+    const uint64_t i = pos[k];
+    if (l >= L || i >= n) { out[k] = kNone; return; }
+    if (l <= 1) { out[k] = i; return; }
+    const uint64_t t = select_bit(u, 0, i, true);            // the (i+1)-th one
+    const uint64_t ch = t - i;                                 // rank0(U, t): its character
+    const uint64_t bp = ch >> (L - l);
+    const uint64_t first = bp << (L - l);                      // smallest character with prefix bp
+    const uint64_t start = first == 0 ? 0 : select_bit(u, 0, first - 1, false) - (first - 1);
+    out[k] = X[(1ull << l) - 2 + bp] + (i - start);
+}
+
+}  // namespace
+}  // namespace wtg
+
+extern "C" {
+
+wt_status wt_wt2wm_size(uint64_t n, uint64_t sigma, size_t *bytes)
+{
+    if (bytes == nullptr) return WT_ERR_INVALID_ARG;
+    wtg::MapLayout m;
+    wt_status st = wtg::map_layout(n, sigma, m);
+    if (st == WT_OK) *bytes = m.bytes;
+    return st;
+}
+
+wt_status wt_wt2wm_build(const uint64_t *d_bv, const void *d_rs, uint64_t n, uint64_t sigma, void *d_map,
+                         size_t map_bytes, void *stream)
+{
+    using namespace wtg;
+    MapLayout m;
+    wt_status st = map_layout(n, sigma, m);
+    if (st != WT_OK) return st;
+    if (d_rs == nullptr || d_map == nullptr || (n > 0 && d_bv == nullptr)) return WT_ERR_INVALID_ARG;
+    if (map_bytes < m.bytes) return WT_ERR_OUT_OF_MEMORY;
+    if (m.L < 2) return WT_OK;                                  // levels 0 and 1 map to themselves
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    QArgs wt = make_args(m.wt, WT_TREE, d_bv, nullptr, d_rs, n);
+    QArgs u = u_args(m, d_map);
+    uint64_t *ubits = const_cast<uint64_t *>(u.bv);
+    k_u_fill<<<(uint32_t)((m.uW + 255) / 256), 256, 0, s>>>(ubits, m.uW, m.ubits);
+    k_u_zeros<<<(uint32_t)(((1ull << (m.L - 1)) + 255) / 256), 256, 0, s>>>(wt, ubits);
+    const dim3 grid((uint32_t)m.unchunks, 1);
+    k_dir_chunks<<<grid, 1024, 0, s>>>(u);
+    k_dir_chunk_scan<<<1, 1024, 0, s>>>(u);
+    k_dir_apply<<<grid, 1024, 0, s>>>(u);
+    uint32_t *X = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(d_map) + m.off_x);
+    for (uint32_t l = 1; l < m.L; ++l) k_x_level<<<1, 1024, 0, s>>>(wt, X, l);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+wt_status wt_wt2wm(const void *d_map, uint64_t n, uint64_t sigma, const uint32_t *d_level, const uint64_t *d_pos,
+                   uint32_t count, uint64_t *d_out, void *stream)
+{
+    using namespace wtg;
+    MapLayout m;
+    wt_status st = map_layout(n, sigma, m);
+    if (st != WT_OK) return st;
+    if (count == 0) return WT_OK;
+    if (d_map == nullptr || d_level == nullptr || d_pos == nullptr || d_out == nullptr) return WT_ERR_INVALID_ARG;
+    QArgs u = u_args(m, const_cast<void *>(d_map));
+    const uint32_t *X = reinterpret_cast<const uint32_t *>(static_cast<const uint8_t *>(d_map) + m.off_x);
+    k_wt2wm<<<(count + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(u, X, m.L, n, d_level, d_pos, count,
+                                                                               d_out);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+}  // extern "C"

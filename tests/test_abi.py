@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "wt
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*\b((?:wt|wm)_[a-z_]+)\s*\(",
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*\b((?:wt|wm)_[a-z0-9_]+)\s*\(",
                        src, flags=re.M)
     return sorted(set(names))
 
