@@ -42,7 +42,11 @@ HBM_FALLBACK_GBS = 6800.0
 # the SHA-256 of the kernel source it was taken on.  The capture ran n = 2^28 (256 MB,
 # above L2) and is scaled to the benchmark's n by symbol count; any later change to
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
-TRAFFIC_CAPTURES = {}
+TRAFFIC_CAPTURES = {
+    # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (profiles/k_build_bs_bytes_n2e28_full.md)
+    "30195a6b4b016f0a71609e38b4ef042a375ef77a0daf3a77af9d3ec3ea8df858": {"dram_bytes": 344495360 + 222899200,
+                                                                         "n": 1 << 28},
+}
 
 
 def kernel_source_hash():
@@ -477,49 +481,120 @@ def run_batched(args):
 # ---------------------------------------------------------------------------
 # served workload: Poisson arrivals into the serving loop
 
+def _serve_once(wtg, reqs, texts, rate, local, warm):
+    """One served run: requests arrive at their Poisson times for `rate` req/s (None:
+    closed loop with 256 requests outstanding, the server's capacity); a consumer
+    thread waits for and releases every result in submission order, so device
+    memory is returned as soon as a result is done.
+    Latency (submit -> completion on the device) is taken per request from
+    wt_server_wait; the first `warm` requests are left out of the statistics."""
+    import queue
+    import threading
+
+    srv = wtg.WtServer(hbm_budget_bytes=64 << 30, max_batch=32, streams=4, device=local)
+    tickets = queue.Queue()
+    lat = []
+    failed = []
+    # closed loop: at most `outstanding` requests submitted and not yet finished
+    outstanding = threading.Semaphore(256 if rate is None else 1 << 30)
+
+    def consume():
+        while True:
+            item = tickets.get()
+            if item is None:
+                return
+            i, tk = item
+            r = srv.wait(tk)
+            if r["status"] != 0:
+                failed.append(i)
+            if i >= warm:
+                lat.append(r["latency_us"])
+            srv.release(tk)
+            outstanding.release()
+
+    th = threading.Thread(target=consume)
+    th.start()
+    sym = 0
+    t0 = time.perf_counter()
+    t_meas = t0
+    for i, (ta, _n, _sg, _zipf, kind, _ts) in enumerate(reqs):
+        if i == warm:
+            t_meas = time.perf_counter()
+        T, sg = texts[i]
+        size = T.numel() if hasattr(T, "numel") else T.size
+        if rate is not None:
+            due = t0 + ta / rate
+            now = time.perf_counter()
+            if due > now:
+                time.sleep(due - now)
+        k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+        outstanding.acquire()
+        tickets.put((i, srv.submit(k, T, sg)))
+        if i >= warm:
+            sym += size
+    tickets.put(None)
+    th.join()
+    wall = time.perf_counter() - t_meas
+    srv.close()
+    lat.sort()
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
+    done = len(reqs) - warm
+    return {"offered_req_per_s": rate, "req_per_s": done / wall, "sym_per_s": sym / wall,
+            "p50_us": q(0.50), "p99_us": q(0.99), "completed": len(lat), "errors": len(failed)}
+
+
 def run_served(args):
+    """Served build: closed-loop capacity, then Poisson arrivals at 0.5, 0.8, 1.0 and
+    1.2 x that capacity (or at --rate alone), each over --requests requests after a
+    warm-up of --served-warmup requests."""
     import torch
     import paper_1702_07578_gb300 as wtg
     import synth
 
     rank, local, world, pg = dist()
     torch.cuda.set_device(local)
-    reqs = synth.request_specs(args.requests, args.rate, max_log=args.served_max_log)
+    warm = args.served_warmup
+    reqs = synth.request_specs(args.requests + warm, 1.0, max_log=args.served_max_log)
     pool = {}
     for i, (_, n, sg, zipf, kind, ts) in enumerate(reqs[: args.pool]):
-        pool[i] = synth.request_text(n, sg, zipf, ts)
-    srv = wtg.WtServer(hbm_budget_bytes=64 << 30, max_batch=32, streams=4, device=local)
-    tickets = []
-    t0 = time.perf_counter()
-    sym = 0
-    for i, (ta, n, sg, zipf, kind, ts) in enumerate(reqs):
-        T = pool[i % args.pool]
-        sgm = reqs[i % args.pool][2]
-        now = time.perf_counter() - t0
-        if ta > now:
-            time.sleep(ta - now)
-        k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
-        tickets.append(srv.submit(k, T, sgm))
-        sym += T.size
-    for tk in tickets:
-        srv.wait(tk)
-        srv.release(tk)
-    wall = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
+        pool[i] = (synth.request_text(n, sg, zipf, ts), sg)
+    texts = [pool[i % args.pool] for i in range(len(reqs))]
+    # client buffers page-locked (wt_server_submit_pinned reads them in place)
+    pinned = {}
+    for i, (T, sg) in pool.items():
+        pinned[i] = (torch.from_numpy(T.view(np.int16) if T.dtype == np.uint16 else T).pin_memory(), sg)
+    ptexts = [pinned[i % args.pool] for i in range(len(reqs))]
+    cap_copy = _serve_once(wtg, reqs, texts, None, local, warm)
+    cap = _serve_once(wtg, reqs, ptexts, None, local, warm)
+    points = []
+    if args.rate is not None:
+        points.append(_serve_once(wtg, reqs, ptexts, args.rate, local, warm))
+    else:
+        for f in (0.5, 0.8, 1.0, 1.2):
+            pt = _serve_once(wtg, reqs, ptexts, f * cap["req_per_s"], local, warm)
+            pt["load"] = f
+            points.append(pt)
     if rank != 0:
         return 0
+    head = next((p for p in points if p.get("load") == 0.8), points[0])
+    mean_n = float(np.mean([t.size for t, _ in texts[warm:]]))
     line = {
         "metric": "served WT/WM construction: symbols/s and latency under Poisson arrivals",
-        "value": sym / wall, "unit": UNIT, "n_gpus": world, "steps": args.requests, "warmup": 0,
-        "ms_per_step": wall * 1e3 / max(args.requests, 1), "higher_is_better": True, "scaling": "weak",
+        "value": head["sym_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.requests, "warmup": warm,
+        "ms_per_step": 1e3 / head["req_per_s"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
-        "config": {"workload": f"Poisson arrivals at {args.rate} req/s, length log-uniform "
-                               f"[2^12, 2^{args.served_max_log}], sigma in {{2^8, 2^16}}, uniform or Zipf(1.0), "
-                               f"WT or WM; {args.pool} distinct texts reused", "hbm_budget": "64 GB",
-                   "requests": args.requests, "max_batch": 32, "streams": 4},
-        "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"]},
-        "completed": st["completed"],
+        "config": {"workload": f"Poisson arrivals, length log-uniform [2^12, 2^{args.served_max_log}] "
+                               f"(mean {mean_n:.3g}), sigma in {{2^8, 2^16}}, uniform or Zipf(1.0), WT or WM; "
+                               f"{args.pool} distinct texts reused", "hbm_budget": "64 GB",
+                   "requests": args.requests, "max_batch": 32, "streams": 4,
+                   "value_at": f"{head.get('load', 'fixed')} x capacity" if "load" in head
+                   else f"{args.rate} req/s",
+                   "submit": "page-locked client buffers read in place (wt_server_submit_pinned); "
+                             "capacity_copy: the copying wt_server_submit"},
+        "latency_us": {"p50": head["p50_us"], "p99": head["p99_us"]},
+        "capacity": cap,
+        "capacity_copy": cap_copy,
+        "sweep": points,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -598,7 +673,10 @@ def main():
     ap.add_argument("--queries", type=int, default=1 << 24)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
-    ap.add_argument("--rate", type=float, default=400.0, help="served: arrivals per second")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="served: one run at this many arrivals per second (default: a sweep "
+                         "at 0.5/0.8/1.0/1.2 x the measured capacity)")
+    ap.add_argument("--served-warmup", type=int, default=64, help="served: requests left out of the statistics")
     ap.add_argument("--pool", type=int, default=128, help="served: distinct texts")
     ap.add_argument("--served-max-log", type=int, default=26)
     ap.add_argument("--n-log2", type=int, default=None,

@@ -223,6 +223,12 @@ wt_status wt_server_create(const wt_server_config *cfg, wt_server **out);
 /* Copy the request's text and queue it; WT_ERR_BUSY if the queue is full or
  * the request alone exceeds the budget.  *ticket identifies it. */
 wt_status wt_server_submit(wt_server *s, const wt_request *req, uint64_t *ticket);
+/* As wt_server_submit, without the host copy: req->h_text must be page-locked
+ * host memory (cudaHostAlloc or cudaHostRegister; anything else gives
+ * WT_ERR_INVALID_ARG) and must stay allocated and unchanged until
+ * wt_server_wait has returned the request as done.  The batch's device copy
+ * reads it directly. */
+wt_status wt_server_submit_pinned(wt_server *s, const wt_request *req, uint64_t *ticket);
 /* Wait until the request is built (timeout_us < 0: no limit); WT_ERR_TIMEOUT
  * if the limit passes first. */
 wt_status wt_server_wait(wt_server *s, uint64_t ticket, int64_t timeout_us, wt_result *res);

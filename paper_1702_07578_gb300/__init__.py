@@ -199,13 +199,25 @@ class WtServer:
         self._keep = {}
 
     def submit(self, kind: int, text, sigma: int) -> int:
+        """Queue a host text.  A numpy array is copied during the call
+        (wt_server_submit); a page-locked torch CPU tensor (``pin_memory()``) is
+        read in place (wt_server_submit_pinned) and is kept referenced here until
+        the request is released."""
         import numpy as np
-        text = np.ascontiguousarray(text)
-        st = {1: WT_U8, 2: WT_U16, 4: WT_U32}[text.dtype.itemsize]
-        req = _native.WtRequest(kind, st, text.ctypes.data if text.size else 0, text.size, int(sigma))
+        if hasattr(text, "is_pinned"):
+            if text.device.type != "cpu" or not text.is_pinned() or not text.is_contiguous():
+                raise ValueError("a tensor text must be a contiguous page-locked CPU tensor")
+            n, width, ptr, fn, keep = text.numel(), text.element_size(), text.data_ptr(), \
+                lib().wt_server_submit_pinned, text
+        else:
+            text = np.ascontiguousarray(text)
+            n, width, ptr, fn, keep = text.size, text.dtype.itemsize, text.ctypes.data, \
+                lib().wt_server_submit, None
+        st = {1: WT_U8, 2: WT_U16, 4: WT_U32}[width]
+        req = _native.WtRequest(kind, st, ptr if n else 0, n, int(sigma))
         t = ctypes.c_uint64(0)
-        _check(lib().wt_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "wt_server_submit")
-        self._keep[t.value] = (kind, text.size, int(sigma))
+        _check(fn(self._h, ctypes.byref(req), ctypes.byref(t)), "wt_server_submit")
+        self._keep[t.value] = (kind, n, int(sigma), keep)
         return t.value
 
     def wait(self, ticket: int, timeout_us: int = -1):
@@ -216,7 +228,7 @@ class WtServer:
 
     def read(self, ticket: int):
         import numpy as np
-        kind, n, sigma = self._keep[ticket]
+        kind, n, sigma, _ = self._keep[ticket]
         L = wt_levels(sigma)
         bv = np.zeros((L, wt_words_per_level(n)), dtype=np.uint64)
         z = np.zeros(max(L, 1), dtype=np.uint64)

@@ -137,6 +137,7 @@ SIGNATURES = {
                                     _C.c_void_p, _C.c_size_t, _C.c_void_p]),
     "wt_server_create": (_C.c_int, [_C.POINTER(WtServerConfig), _C.POINTER(_C.c_void_p)]),
     "wt_server_submit": (_C.c_int, [_C.c_void_p, _C.POINTER(WtRequest), _C.POINTER(_C.c_uint64)]),
+    "wt_server_submit_pinned": (_C.c_int, [_C.c_void_p, _C.POINTER(WtRequest), _C.POINTER(_C.c_uint64)]),
     "wt_server_wait": (_C.c_int, [_C.c_void_p, _C.c_uint64, _C.c_int64, _C.POINTER(WtResult)]),
     "wt_server_release": (_C.c_int, [_C.c_void_p, _C.c_uint64]),
     "wt_server_read": (_C.c_int, [_C.c_void_p, _C.c_uint64, _C.c_void_p, _C.c_void_p]),

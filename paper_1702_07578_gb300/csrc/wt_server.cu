@@ -33,7 +33,8 @@ struct Req {
     wt_symtype type = WT_U8;
     uint64_t n = 0, sigma = 0;
     uint32_t L = 0;
-    std::vector<uint8_t> host;        // text copy (freed once on the device)
+    std::unique_ptr<uint8_t[]> host;  // text copy (freed once on the device)
+    const void *src = nullptr;        // host.get(), or the caller's page-locked text
     void *d_text = nullptr;
     uint64_t *d_bv = nullptr;
     uint64_t *d_zeros = nullptr;
@@ -118,7 +119,7 @@ void launch_batch(wt_server *s, Batch *b)
             status = WT_ERR_OUT_OF_MEMORY;
             break;
         }
-        if (cudaMemcpyAsync(r->d_text, r->host.data(), r->n * (size_t)r->type, cudaMemcpyHostToDevice, st) !=
+        if (cudaMemcpyAsync(r->d_text, r->src, r->n * (size_t)r->type, cudaMemcpyHostToDevice, st) !=
             cudaSuccess) {
             status = WT_ERR_CUDA;
             break;
@@ -166,7 +167,8 @@ void finish_batch(wt_server *s, Batch *b)   // lock held
         r->done = true;
         r->status = b->status;
         r->t_done = now;
-        std::vector<uint8_t>().swap(r->host);
+        r->host.reset();
+        r->src = nullptr;
         // the workspace share of the reservation is returned now
         s->in_use -= r->ws_alone;
         r->reserved -= r->ws_alone;
@@ -250,11 +252,25 @@ wt_status wt_server_create(const wt_server_config *cfg, wt_server **out)
     return WT_OK;
 }
 
-wt_status wt_server_submit(wt_server *s, const wt_request *req, uint64_t *ticket)
+}  // extern "C"
+
+namespace {
+
+// Queues a request; `borrowed`: the text is the caller's page-locked buffer,
+// read by the device copy of the batch, and must stay unchanged until the
+// request is done.
+wt_status submit_impl(wt_server *s, const wt_request *req, uint64_t *ticket, bool borrowed)
 {
     if (s == nullptr || req == nullptr || ticket == nullptr) return WT_ERR_INVALID_ARG;
     if (req->kind != WT_TREE && req->kind != WT_MATRIX) return WT_ERR_INVALID_ARG;
     if (req->n > 0 && req->h_text == nullptr) return WT_ERR_INVALID_ARG;
+    if (borrowed && req->n > 0) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, req->h_text) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return WT_ERR_INVALID_ARG;
+        }
+    }
     auto r = std::make_shared<Req>();
     r->kind = req->kind;
     r->type = req->type;
@@ -270,8 +286,15 @@ wt_status wt_server_submit(wt_server *s, const wt_request *req, uint64_t *ticket
         return WT_ERR_BUSY;
     }
     lk.unlock();
-    r->host.resize(req->n * (size_t)req->type);
-    if (req->n) std::memcpy(r->host.data(), req->h_text, r->host.size());
+    if (borrowed) {
+        r->src = req->h_text;
+    } else if (req->n) {
+        const size_t bytes = req->n * (size_t)req->type;
+        r->host.reset(new (std::nothrow) uint8_t[bytes]);     // no value-initialisation
+        if (!r->host) return WT_ERR_OUT_OF_MEMORY;
+        std::memcpy(r->host.get(), req->h_text, bytes);
+        r->src = r->host.get();
+    }
     lk.lock();
     r->ticket = s->next_ticket++;
     r->t_submit = Clock::now();
@@ -282,6 +305,20 @@ wt_status wt_server_submit(wt_server *s, const wt_request *req, uint64_t *ticket
     *ticket = r->ticket;
     s->cv_sched.notify_all();
     return WT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wt_status wt_server_submit(wt_server *s, const wt_request *req, uint64_t *ticket)
+{
+    return submit_impl(s, req, ticket, false);
+}
+
+wt_status wt_server_submit_pinned(wt_server *s, const wt_request *req, uint64_t *ticket)
+{
+    return submit_impl(s, req, ticket, true);
 }
 
 wt_status wt_server_wait(wt_server *s, uint64_t ticket, int64_t timeout_us, wt_result *res)

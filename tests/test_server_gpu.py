@@ -80,3 +80,34 @@ def test_wait_timeout_returns():
     assert srv.wait(t, 60_000_000)["status"] == 0
     srv.release(t)
     srv.close()
+
+
+def test_pinned_submit_matches_copy_submit():
+    """wt_server_submit_pinned reads page-locked client buffers in place; results
+    equal the copying submit and the oracle; a pageable tensor is refused."""
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    reqs = _requests(12, 91, max_log=17)
+    srv = wtg.WtServer(hbm_budget_bytes=2 << 30, max_batch=4, streams=2)
+    pinned = [torch.from_numpy(T.view(np.int16) if T.dtype == np.uint16 else T).pin_memory()
+              for _, T, _ in reqs]
+    tp = [srv.submit(wtg.WT_TREE if k == "wt" else wtg.WT_MATRIX, P, sg)
+          for (k, _, sg), P in zip(reqs, pinned)]
+    tc = [srv.submit(wtg.WT_TREE if k == "wt" else wtg.WT_MATRIX, T, sg) for k, T, sg in reqs]
+    for (k, T, sg), a, b in zip(reqs, tp, tc):
+        assert srv.wait(a)["status"] == 0 and srv.wait(b)["status"] == 0
+        bva, za = srv.read(a)
+        bvb, zb = srv.read(b)
+        srv.release(a)
+        srv.release(b)
+        assert np.array_equal(bva, bvb)
+        if k == "wt":
+            assert np.array_equal(bva, oracle.wt(T, sg))
+        else:
+            e, ez = oracle.wm(T, sg)
+            assert np.array_equal(bva, e) and np.array_equal(za, ez) and np.array_equal(zb, ez)
+    pageable = torch.from_numpy(reqs[0][1].astype(np.uint8) if reqs[0][2] <= 256 else reqs[0][1].view(np.int16))
+    with pytest.raises(ValueError):
+        srv.submit(wtg.WT_TREE, pageable, reqs[0][2])
+    srv.close()
