@@ -93,6 +93,21 @@ wt_status wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sig
  * this workspace during the last build on it (WT_OK if none), then clear it. */
 wt_status wt_sync_status(void *d_ws, void *stream);
 
+/* ---- the wavelet tree and the wavelet matrix of one text, together ------------
+ * Level l of the WT and level l of the WM hold the same bits interval by
+ * interval: both are stable splits of the same symbols, and only the order of
+ * the intervals in the level differs (id order for the WT, bit-reversal order
+ * for the WM, Sec. 5.1 and Sec. 5.2).  wt_wm_build builds both from one
+ * histogram pass and one split pass over the text when sigma <= 256 and
+ * n > 4096: every tile's class runs are split once and written to both.
+ * Otherwise it runs wt_build and then wm_build on the stream.  The output is
+ * bit-identical to wt_build (d_bv_wt) plus wm_build (d_bv_wm, d_zeros); the
+ * arguments, limits and errors are theirs (wt_sync_status reads device
+ * errors).  The workspace is wt_wm_workspace_size bytes. */
+wt_status wt_wm_workspace_size(wt_symtype type, uint64_t n, uint64_t sigma, size_t *bytes);
+wt_status wt_wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv_wt,
+                      uint64_t *d_bv_wm, uint64_t *d_zeros, void *d_ws, size_t ws_bytes, void *stream);
+
 /* ---- wavelet tree without any device allocation --------------------------
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code running under a host

@@ -124,6 +124,34 @@ def wm_build(text, sigma: int, bv=None, zeros=None, ws=None, stream=None):
     return bv, zeros[:wt_levels(sigma)]
 
 
+def wt_wm_workspace_size(symtype: int, n: int, sigma: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().wt_wm_workspace_size(symtype, int(n), int(sigma), ctypes.byref(out)), "wt_wm_workspace_size")
+    return out.value
+
+
+def wt_wm_build(text, sigma: int, bv_wt=None, bv_wm=None, zeros=None, ws=None, stream=None):
+    """WT and WM of the same device text in one call; returns (WT bits, WM bits, Z)."""
+    torch = _torch()
+    if not text.is_cuda or not text.is_contiguous():
+        raise ValueError("text must be a contiguous CUDA tensor")
+    n = text.numel()
+    L = wt_levels(sigma)
+    W = wt_words_per_level(n)
+    dev = text.device
+    if bv_wt is None:
+        bv_wt = torch.empty((L, W), dtype=torch.int64, device=dev)
+    if bv_wm is None:
+        bv_wm = torch.empty((L, W), dtype=torch.int64, device=dev)
+    if zeros is None:
+        zeros = torch.empty((max(L, 1),), dtype=torch.int64, device=dev)
+    if ws is None:
+        ws = torch.empty((max(wt_wm_workspace_size(_symtype(text), n, sigma), 1),), dtype=torch.uint8, device=dev)
+    _check(lib().wt_wm_build(_ptr(text), _symtype(text), n, int(sigma), _ptr(bv_wt), _ptr(bv_wm), _ptr(zeros),
+                             _ptr(ws), ws.numel(), _stream(stream)), "wt_wm_build")
+    return bv_wt, bv_wm, zeros[:L]
+
+
 def wt_sync_status(ws, stream=None):
     """Synchronise and raise WtError if the device recorded an error in ws."""
     _check(lib().wt_sync_status(_ptr(ws), _stream(stream)), "device")

@@ -14,6 +14,7 @@ struct HostText {
     uint64_t sigma;
     uint64_t *bv;
     uint64_t *zeros;
+    uint64_t *bv2 = nullptr;     // kBoth: the WM's levels (bv holds the WT's)
 };
 
 struct Plan {
@@ -53,7 +54,8 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
                     Plan &p, uint32_t spb = 0)
 {
     if (!valid_spb(spb)) return WT_ERR_INVALID_ARG;
-    if (kind != WT_TREE && kind != WT_MATRIX) return WT_ERR_INVALID_ARG;
+    const bool both = (uint32_t)kind == kBoth;
+    if (kind != WT_TREE && kind != WT_MATRIX && !both) return WT_ERR_INVALID_ARG;
     if (type != WT_U8 && type != WT_U16 && type != WT_U32) return WT_ERR_INVALID_ARG;
     if (count > 0 && t == nullptr) return WT_ERR_INVALID_ARG;
     const uint32_t w = (uint32_t)type;
@@ -71,16 +73,19 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
         if (x.sigma > (1ull << 32)) return WT_ERR_INVALID_ARG;
         const uint32_t L = levels_of(x.sigma);
         if (kind == WT_TREE && L > (uint32_t)kMaxTreeSigmaLog) return WT_ERR_INVALID_ARG;
+        if (both && (L > (uint32_t)kChunk || (x.n > 0 && x.n <= kSmallJob))) return WT_ERR_INVALID_ARG;
         if (check_ptrs && L > 0) {
             if (x.n > 0 && (x.text == nullptr || x.bv == nullptr)) return WT_ERR_INVALID_ARG;
-            if (kind == WT_MATRIX && x.zeros == nullptr) return WT_ERR_INVALID_ARG;
+            if ((kind == WT_MATRIX || both) && x.zeros == nullptr) return WT_ERR_INVALID_ARG;
+            if (both && (x.bv2 == nullptr || reinterpret_cast<uintptr_t>(x.bv2) % 8)) return WT_ERR_INVALID_ARG;
             if (reinterpret_cast<uintptr_t>(x.text) % w) return WT_ERR_INVALID_ARG;
             if (reinterpret_cast<uintptr_t>(x.bv) % 8) return WT_ERR_INVALID_ARG;
         }
         TextInfo &ti = p.texts[i];
         ti.text = x.text;
         ti.bv = x.bv;
-        ti.zeros = kind == WT_MATRIX ? x.zeros : nullptr;
+        ti.bv2 = both ? x.bv2 : nullptr;
+        ti.zeros = (kind == WT_MATRIX || both) ? x.zeros : nullptr;
         ti.n = x.n;
         ti.W = (x.n + 63) / 64;
         ti.sigma = x.sigma;
@@ -202,7 +207,8 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + p.off_ctl);
     TextInfo *dtexts = reinterpret_cast<TextInfo *>(ws + p.off_texts);
     if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) return WT_ERR_CUDA;
-    if (kind == WT_MATRIX && launch_zero_z(dtexts, p.count, s) != cudaSuccess) return WT_ERR_CUDA;
+    if ((kind == WT_MATRIX || (uint32_t)kind == kBoth) && launch_zero_z(dtexts, p.count, s) != cudaSuccess)
+        return WT_ERR_CUDA;
     for (uint32_t r = 0; r < p.rounds; ++r) {
         RoundArgs a{};
         a.ctl = ctl;
@@ -300,6 +306,45 @@ wt_status wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sig
                    uint64_t *d_zeros, void *d_ws, size_t ws_bytes, void *stream)
 {
     return single(WT_MATRIX, d_text, type, n, sigma, d_bv, d_zeros, d_ws, ws_bytes, stream);
+}
+
+namespace {
+
+// The fused pass applies to a text with L <= 8 and more than kSmallJob symbols.
+bool fused_fits(uint64_t n, uint64_t sigma) { return levels_of(sigma) <= (uint32_t)kChunk && n > kSmallJob; }
+
+}  // namespace
+
+wt_status wt_wm_workspace_size(wt_symtype type, uint64_t n, uint64_t sigma, size_t *bytes)
+{
+    if (bytes == nullptr) return WT_ERR_INVALID_ARG;
+    if (sigma > 0 && n < (1ull << 32) && fused_fits(n, sigma)) {
+        HostText h{nullptr, n, sigma, nullptr, nullptr};
+        Plan p;
+        wt_status st = make_plan(static_cast<wt_kind>(kBoth), type, &h, 1, false, p, kMinSpb);
+        if (st == WT_OK) *bytes = p.bytes;
+        return st;
+    }
+    size_t a = 0, b = 0;
+    wt_status st = wt_workspace_size(WT_TREE, type, n, sigma, &a);
+    if (st == WT_OK) st = wt_workspace_size(WT_MATRIX, type, n, sigma, &b);
+    if (st == WT_OK) *bytes = a > b ? a : b;
+    return st;
+}
+
+wt_status wt_wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv_wt,
+                      uint64_t *d_bv_wm, uint64_t *d_zeros, void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (sigma == 0 || n >= (1ull << 32) || !fused_fits(n, sigma)) {
+        wt_status st = single(WT_TREE, d_text, type, n, sigma, d_bv_wt, nullptr, d_ws, ws_bytes, stream);
+        if (st != WT_OK) return st;
+        return single(WT_MATRIX, d_text, type, n, sigma, d_bv_wm, d_zeros, d_ws, ws_bytes, stream);
+    }
+    HostText h{d_text, n, sigma, d_bv_wt, d_zeros, d_bv_wm};
+    Plan p;
+    wt_status st = make_plan(static_cast<wt_kind>(kBoth), type, &h, 1, true, p);
+    if (st != WT_OK) return st;
+    return run_plan(static_cast<wt_kind>(kBoth), p, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 wt_status wt_sync_status(void *d_ws, void *stream)

@@ -27,6 +27,13 @@ constexpr int kCols = 256;            // histogram columns (2^8 classes per roun
 constexpr int kMaxTreeSigmaLog = 24;  // WT alphabets up to 2^24
 constexpr int kTileSyms = 32768;      // symbols per tile of the bit-sliced build; groups are multiples
 
+// RoundArgs::kind besides WT_TREE / WT_MATRIX: the WT and the WM of the same
+// texts in one pass (texts with L <= 8 and more than kSmallJob symbols).  Within a
+// tile both are the same stable splits (WM order); only the intervals' places
+// in the levels differ, so every class run is written twice.
+constexpr uint32_t kBoth = 2;
+constexpr uint32_t kSmallJob = 4096;  // jobs of the last round up to this size: one warp each
+
 // Default symbols per build block: two tiles.
 constexpr uint32_t kDefaultGroup = 2 * 32768;
 
@@ -36,8 +43,9 @@ __host__ __device__ inline uint32_t width_for_bits(uint32_t b) { return b <= 8 ?
 struct TextInfo {
     const void *text;        // caller's symbols (round 0 input)
     void *buf[2];            // re-sorted symbols: round r writes buf[r & 1]
-    uint64_t *bv;            // L * W words
-    uint64_t *zeros;         // WM: L values
+    uint64_t *bv;            // L * W words (the WT's when kind == kBoth)
+    uint64_t *bv2;           // kBoth: the WM's L * W words
+    uint64_t *zeros;         // WM (and kBoth): L values
     uint64_t n;
     uint64_t W;
     uint64_t sigma;
@@ -79,7 +87,7 @@ struct RoundArgs {
     uint32_t nslots;         // slots in this round
     uint32_t pnslots;        // slots in the previous round
     uint32_t round;
-    uint32_t kind;           // WT_TREE / WT_MATRIX
+    uint32_t kind;           // WT_TREE / WT_MATRIX / kBoth
     uint32_t gelems;         // symbols per group in this round
     uint32_t groups_ub;      // grid bound for per-group kernels
     uint32_t blocks_ub;      // grid bound for per-block kernels

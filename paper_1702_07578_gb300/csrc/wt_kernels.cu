@@ -78,7 +78,7 @@ __device__ __forceinline__ RoundText round_text(const TextInfo &t, uint32_t r)
 // Jobs of the last round of their text with at most kSmallJob symbols are built
 // by one warp each (k_build_small) and get no groups.
 constexpr uint32_t kSmallWords = 4;                  // words per lane of the warp build
-constexpr uint32_t kSmallJob = 32 * 32 * kSmallWords;   // 4096 symbols
+static_assert(kSmallJob == 32 * 32 * kSmallWords, "a small job is one warp's 32 x 32 x kSmallWords bits");
 
 __device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uint64_t n)
 {
@@ -298,16 +298,14 @@ __global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
 // ---------------------------------------------------------------------------
 // a1: class histogram of every group (the first counting-sort phase)
 
-// Two sub-histograms per warp (even and odd lanes), 257 words apart so that
-// equal classes of the two copies fall in different banks: with skewed texts
-// (Zipf) many lanes of a warp count the same class at once.
-constexpr int kHistThreads = 512;
-constexpr int kHistWarps = kHistThreads / 32;
-constexpr int kHistCopies = 2;
-constexpr int kHistStride = kCols + 1;
-constexpr size_t kHistSmem = sizeof(uint32_t) * kHistWarps * kHistCopies * kHistStride;
+// One histogram per block, shared by all its warps.  Measured on the byte
+// workload: per-warp copies cost more in their per-tile reduction (every tile
+// row sums all copies) and in shared memory per block than they save in
+// same-class atomics, and small blocks (8 per SM) keep more loads in flight.
+constexpr int kHistThreads = 256;
+constexpr size_t kHistSmem = sizeof(uint32_t) * kCols;
 
-__global__ void __launch_bounds__(kHistThreads, 3) k_hist(RoundArgs a)
+__global__ void __launch_bounds__(kHistThreads, 8) k_hist(RoundArgs a)
 {
     extern __shared__ __align__(16) uint32_t wh[];
     const uint32_t g = blockIdx.x;
@@ -321,14 +319,14 @@ __global__ void __launch_bounds__(kHistThreads, 3) k_hist(RoundArgs a)
     const uint32_t shift = rt.rb - rt.h, mask = (1u << rt.h) - 1u;
     const bool check = a.round == 0 && t.sigma < (1ull << t.L);
     const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
-    uint32_t *mine = wh + ((threadIdx.x >> 5) * kHistCopies + (threadIdx.x & (kHistCopies - 1))) * kHistStride;
+    uint32_t *mine = wh;
     bool bad = false;
     const uint8_t *base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
     const uint32_t top = a.round == 0 && t.L < 8 ? (0xffu << t.L) & 0xffu : 0u;
     const uint32_t top4 = top * 0x01010101u;
     const uint32_t tile_first = jb.tile0 + (uint32_t)(g0 / kTileSyms);
     uint32_t gsum = 0;                                   // running group count of column threadIdx.x
-    for (uint32_t i = threadIdx.x; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) wh[i] = 0;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kCols; i += kHistThreads) wh[i] = 0;
     __syncthreads();
     // one tile (kTileSyms symbols) at a time; a tile's row is the difference of
     // the running counts after and before it
@@ -374,18 +372,16 @@ __global__ void __launch_bounds__(kHistThreads, 3) k_hist(RoundArgs a)
             });
         }
         __syncthreads();
-        if (threadIdx.x < (uint32_t)kCols) {
-            const uint32_t col = threadIdx.x;
-            uint32_t s = 0;
-#pragma unroll 8
-            for (int c = 0; c < kHistWarps * kHistCopies; ++c) s += wh[c * kHistStride + col];
-            a.thist[((size_t)tile_first + tix) * kCols + col] = s - gsum;
+        static_assert(kHistThreads == kCols, "one column per thread");
+        {
+            const uint32_t s = wh[threadIdx.x];
+            a.thist[((size_t)tile_first + tix) * kCols + threadIdx.x] = s - gsum;
             gsum = s;
         }
         __syncthreads();
     }
     if (bad) atomicCAS(&a.ctl->status, 0u, (uint32_t)WT_ERR_SYMBOL_RANGE);
-    if (threadIdx.x < (uint32_t)kCols) a.ghist[(size_t)g * kCols + threadIdx.x] = gsum;
+    a.ghist[(size_t)g * kCols + threadIdx.x] = gsum;
 }
 
 // ---------------------------------------------------------------------------
@@ -510,7 +506,10 @@ struct BsSmem {
     uint32_t lvl[kBsWords + 4];               // the current level's plane, tile order
     uint32_t wsum[kWarps];                    // zeros of each warp's range
     uint32_t thc[kCols];                      // class counts of the tile (histogram pass)
-    uint16_t cntw[kWarps][kCols];             // cut: class counts / offsets per warp chunk
+    union {
+        uint16_t cntw[kWarps][kCols];         // cut: class counts / offsets per warp chunk
+        uint8_t wcls2[kChunk][kBsWords / 2 + 2 * kCols];  // kBoth: wcls of the WM
+    };
     uint8_t wcls[kChunk][kBsWords / 2 + 2 * kCols];   // destination word -> class, per level
     uint32_t tP[kCols + 1];
     uint32_t offq[kCols];                     // class counts of the job before this tile
@@ -523,7 +522,15 @@ struct BsSmem {
     uint32_t glo[kHeap];                      // class start inside the text's level (bits)
     uint32_t wpre[kHeap];                     // destination words before each class
     uint32_t wtot[kChunk + 2];
+    uint32_t jspos2[kHeap];                   // kBoth: the WM's jspos, glo, wpre, wtot
+    uint32_t glo2[kHeap];
+    uint32_t wpre2[kHeap];
+    uint32_t wtot2[kChunk + 2];
 };
+
+// Two blocks per SM: each block's shared memory (plus the 1 KB the hardware
+// reserves per block) must fit in half of the SM's 228 KB.
+static_assert(sizeof(BsSmem) + 1024 <= 114 * 1024, "k_build_bs needs two blocks per SM");
 
 // x * c as an integer multiply.  The left shifts of the move-vector computation
 // are written this way so that they issue on the multiply-add pipe, which this
@@ -687,6 +694,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const uint32_t shift = rb - h;                   // > 0 in rounds with a cut
     const uint32_t gi = g - jb.g0;
     const bool matrix = a.kind == WT_MATRIX;
+    const bool both = a.kind == kBoth;
 
     // job totals -> class totals and interval starts of every level (fold,
     // Alg. 1; zero-based prefix sums in id or pi_l order, Sec. 3.1 / 5.1)
@@ -707,13 +715,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         if (l <= h) sm.jcnt[idx] = sm.jP[(q + 1) << (h - l)] - sm.jP[q << (h - l)];
     }
     __syncthreads();
-    if (warp <= h) {
-        const uint32_t l = warp, base = 1u << l;
+    for (uint32_t j = warp; j < (h + 1) * (both ? 2u : 1u); j += kWarps) {
+        const uint32_t l = j % (h + 1), base = 1u << l;   // j > h: the WM's starts (kBoth)
+        const bool rv = matrix || j > h;
+        uint32_t *dst = j > h ? sm.jspos2 : sm.jspos;
         warp_scan_256(base, [&](uint32_t q) { return sm.jcnt[base + q]; },
-                      [&](uint32_t i) { return matrix ? rev_bits(i, l) : i; },
-                      [&](uint32_t q, uint32_t v) { sm.jspos[base + q] = v; });
+                      [&](uint32_t i) { return rv ? rev_bits(i, l) : i; },
+                      [&](uint32_t q, uint32_t v) { dst[base + q] = v; });
     }
-    if (matrix && gi == 0 && tid < h) {              // Z[c + l]: even (l+1)-prefixes
+    if ((matrix || both) && gi == 0 && tid < h) {    // Z[c + l]: even (l+1)-prefixes
         const uint32_t l = tid, base = 2u << l;
         uint32_t z = 0;
         for (uint32_t p = 0; p < base; p += 2) z += sm.jcnt[base + p];
@@ -755,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 const uint32_t s = h - l, lo = q << s, hi = (q + 1) << s;
                 sm.cnt[idx] = sm.tP[hi] - sm.tP[lo];
                 sm.glo[idx] = jb.off + sm.jspos[idx] + (sm.oP[hi] - sm.oP[lo]);
+                if (both) sm.glo2[idx] = jb.off + sm.jspos2[idx] + (sm.oP[hi] - sm.oP[lo]);
             }
         }
         __syncthreads();
@@ -766,28 +777,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                           [&](uint32_t i) { return rev_bits(i, h); },
                           [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
         }
-        if (warp < h) {
+        if (warp < h) {                             // class starts in tile order (shared by kBoth)
             const uint32_t l = warp, base = 1u << l;
             warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
                           [&](uint32_t i) { return rev_bits(i, l); },
                           [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
+        }
+        if (warp < h || (both && warp < 2 * h)) {  // destination words: warp h + l does the WM's (kBoth)
+            const bool second = warp >= h;
+            const uint32_t l = second ? warp - h : warp, base = 1u << l;
+            const uint32_t *glo = second ? sm.glo2 : sm.glo;
+            uint32_t *wpre = second ? sm.wpre2 : sm.wpre;
             const uint32_t wt = warp_scan_256(
                 base,
                 [&](uint32_t q) {
                     const uint32_t c = sm.cnt[base + q];
                     if (c == 0) return 0u;
-                    const uint32_t gs = sm.glo[base + q];
+                    const uint32_t gs = glo[base + q];
                     return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
                 },
-                [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[base + q] = v; });
-            if (lane == 0) sm.wtot[l] = wt;
+                [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { wpre[base + q] = v; });
+            if (lane == 0) (second ? sm.wtot2 : sm.wtot)[l] = wt;
             // word -> class map of level l: every nonempty class marks its first
             // destination word, a running maximum fills the words after it
-            uint8_t *wc = sm.wcls[l];
+            uint8_t *wc = second ? sm.wcls2[l] : sm.wcls[l];
             for (uint32_t k = lane; k < wt; k += 32) wc[k] = 0;
             __syncwarp();
             for (uint32_t q = lane; q < base; q += 32)
-                if (sm.cnt[base + q]) wc[sm.wpre[base + q]] = (uint8_t)q;
+                if (sm.cnt[base + q]) wc[wpre[base + q]] = (uint8_t)q;
             __syncwarp();
             const uint32_t per = (wt + 31) / 32, b0 = lane * per, b1 = min(wt, b0 + per);
             uint32_t mx = 0;
@@ -847,14 +864,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint32_t zo = __shfl_sync(kFull, wex, warp) + zl;
 
 
-            // copy every class's bits to its interval start in level c + l
-            {
-                const uint32_t wt = sm.wtot[l];
-                uint64_t *lv = t.bv + (uint64_t)(rt.c + l) * t.W;
+            // copy every class's bits to its interval start in level c + l (for
+            // kBoth: in the WT's levels, then in the WM's)
+            for (uint32_t out = 0; out < (both ? 2u : 1u); ++out) {
+                const uint32_t wt = out ? sm.wtot2[l] : sm.wtot[l];
+                const uint8_t *wc = out ? sm.wcls2[l] : sm.wcls[l];
+                const uint32_t *glo = out ? sm.glo2 : sm.glo;
+                const uint32_t *wpre = out ? sm.wpre2 : sm.wpre;
+                uint64_t *lv = (out ? t.bv2 : t.bv) + (uint64_t)(rt.c + l) * t.W;
                 for (uint32_t k = tid; k < wt; k += kThreads) {
-                    const uint32_t idx = base + sm.wcls[l][k];
-                    const uint64_t gs = sm.glo[idx], ge = gs + sm.cnt[idx];
-                    const uint64_t word = (gs >> 6) + (k - sm.wpre[idx]);
+                    const uint32_t idx = base + wc[k];
+                    const uint64_t gs = glo[idx], ge = gs + sm.cnt[idx];
+                    const uint64_t word = (gs >> 6) + (k - wpre[idx]);
                     const uint64_t wb = word << 6;
                     const uint32_t blo = (uint32_t)((gs > wb ? gs : wb) - wb);
                     uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
@@ -1196,10 +1217,10 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
     if (prof) { profile_mark(2, false, s); profile_mark(0, true, s); }
     k_build_bs<<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
-    if (a.any_plain)
+    if (a.any_plain && a.kind != kBoth)           // kBoth has no small jobs
         k_build_small<<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
                         sizeof(SmallSmem) * kSmallWarps, s>>>(a);
-    if (prof) profile_mark(0, false, s, a.any_plain ? 2 : 1);
+    if (prof) profile_mark(0, false, s, (a.any_plain && a.kind != kBoth) ? 2 : 1);
     return cudaGetLastError();
 }
 
