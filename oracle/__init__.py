@@ -15,6 +15,8 @@ uint64, level-major, bit j of a level at bit ``j & 63`` of word ``j >> 6``):
 ``pc(kind, T, sigma)``      Algorithm 1, pcWT / pcWM (Sec. 3.1, Sec. 5.1)
 ``ps(kind, T, sigma, p)``   Algorithm 2, psWT / psWM with p slices (Sec. 3.2.1)
 ``wt2wm(T, sigma, l, i)``   Lemma 3: WT position -> WM position (``lemma3.py``, numpy)
+``stable_order(T, sigma, kind)``  the order after the last level, as a permutation and
+                            as the sorted text (``order.py``, numpy)
 """
 from __future__ import annotations
 
@@ -146,3 +148,4 @@ def bits_string(bv_level, n):
 
 
 from .lemma3 import wt2wm, wt2wm_tables  # noqa: E402,F401
+from .order import stable_order  # noqa: E402,F401
