@@ -645,6 +645,72 @@ def run_served(args):
 
 
 # ---------------------------------------------------------------------------
+# order: the stable order after the last level as a by-product of the builds
+
+def run_order(args):
+    """Per step: wt_build_order + wm_build_order of the resident text (levels,
+    permutation and sorted text of both), against wt_build + wm_build."""
+    import torch
+    import paper_1702_07578_gb300 as wtg
+
+    rank, local, world, pg = dist()
+    torch.cuda.set_device(local)
+    T, sigma, desc = load_workload("bytes", args.n_log2)
+    n, w = T.size, T.dtype.itemsize
+    L = wtg.wt_levels(sigma)
+    text = torch.from_numpy(T).cuda()
+    ws = {k: torch.empty((wtg.wt_order_workspace_size(k, w, n, sigma),), dtype=torch.uint8, device="cuda")
+          for k in (wtg.WT_TREE, wtg.WT_MATRIX)}
+    outs = {}
+    stream = torch.cuda.current_stream()
+
+    def order_step():
+        for k in (wtg.WT_TREE, wtg.WT_MATRIX):
+            outs[k] = wtg.build_order(k, text, sigma, ws=ws[k], stream=stream)
+
+    def plain_step():
+        wtg.wt_build(text, sigma, ws=ws[wtg.WT_TREE], stream=stream)
+        wtg.wm_build(text, sigma, ws=ws[wtg.WT_MATRIX], stream=stream)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        barrier(pg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
+
+    ms = timed(order_step)
+    for k in ws:
+        wtg.wt_sync_status(ws[k])
+    plain_ms = timed(plain_step)
+    # spot check against the definition on a sample: perm is a stable sort by the key
+    p = outs[wtg.WT_TREE][2][: 1 << 20].cpu().numpy().view(np.uint32).astype(np.int64)
+    srt = outs[wtg.WT_TREE][3][: 1 << 20].cpu().numpy()
+    assert np.array_equal(T[p], srt) and np.all(np.diff(srt.astype(np.int64)) >= 0)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "input symbols/s, WT+WM construction with the stable order (permutation + sorted text)",
+        "value": world * 2 * n / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8" if w == 1 else f"u{8 * w}", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "sigma": sigma, "levels": L, "builds_per_step": 2,
+                   "outputs": "levels, Z, uint32 permutation, sorted text (WT and WM)",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "plain_ms_per_step": plain_ms,
+        "order_overhead": ms / plain_ms - 1.0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # queries: access / rank / select on the built 2^30-symbol WT and WM
 
 def run_queries(args):
@@ -713,7 +779,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bytes",
-                    choices=["bytes", "small", "large_alphabet", "batched", "served", "queries"])
+                    choices=["bytes", "small", "large_alphabet", "batched", "served", "queries", "order"])
     ap.add_argument("--queries", type=int, default=1 << 24)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
@@ -738,6 +804,8 @@ def main():
         return run_served(args)
     if args.workload == "queries":
         return run_queries(args)
+    if args.workload == "order":
+        return run_order(args)
     return run_ours(args)
 
 

@@ -93,6 +93,27 @@ wt_status wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sig
  * this workspace during the last build on it (WT_OK if none), then clear it. */
 wt_status wt_sync_status(void *d_ws, void *stream);
 
+/* ---- the stable order as a by-product ----------------------------------------
+ * The splits that build the levels leave the symbols, after the last level, in
+ * one stable order (Obs. 1 and Obs. 2 one level past the last): for the WT, T
+ * stably sorted by symbol (the sorted text psWT builds level by level,
+ * Sec. 3.2.1); for the WM, T stably sorted by the bit-reversed L-bit code.
+ * wt_build_order / wm_build_order build the levels (bit-identical to wt_build /
+ * wm_build) and also write
+ *   d_perm[j]    text position of the j-th symbol in that order (n uint32,
+ *                required when n > 0)
+ *   d_sorted[j]  T[d_perm[j]] (n symbols of the text's type; may be NULL).
+ * For sigma = 1 the order is the text order.  The workspace is
+ * wt_order_workspace_size bytes (it adds n uint32 of positions carried through
+ * each round that cuts).  Texts that want the order take the block path for
+ * every job, also for jobs of at most 4096 symbols. */
+wt_status wt_order_workspace_size(wt_kind kind, wt_symtype type, uint64_t n, uint64_t sigma, size_t *bytes);
+wt_status wt_build_order(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv,
+                         uint32_t *d_perm, void *d_sorted, void *d_ws, size_t ws_bytes, void *stream);
+wt_status wm_build_order(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv,
+                         uint64_t *d_zeros, uint32_t *d_perm, void *d_sorted, void *d_ws, size_t ws_bytes,
+                         void *stream);
+
 /* ---- the wavelet tree and the wavelet matrix of one text, together ------------
  * Level l of the WT and level l of the WM hold the same bits interval by
  * interval: both are stable splits of the same symbols, and only the order of

@@ -124,6 +124,38 @@ def wm_build(text, sigma: int, bv=None, zeros=None, ws=None, stream=None):
     return bv, zeros[:wt_levels(sigma)]
 
 
+def wt_order_workspace_size(kind: int, symtype: int, n: int, sigma: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().wt_order_workspace_size(kind, symtype, int(n), int(sigma), ctypes.byref(out)),
+           "wt_order_workspace_size")
+    return out.value
+
+
+def build_order(kind: int, text, sigma: int, sorted_text: bool = True, ws=None, stream=None):
+    """WT (kind WT_TREE) or WM (WT_MATRIX) of a device text plus the stable order
+    after the last level: returns (bit vectors, Z or None, perm, sorted text or None)."""
+    torch = _torch()
+    if not text.is_cuda or not text.is_contiguous():
+        raise ValueError("text must be a contiguous CUDA tensor")
+    n = text.numel()
+    L = wt_levels(sigma)
+    dev = text.device
+    bv = torch.empty((L, wt_words_per_level(n)), dtype=torch.int64, device=dev)
+    zeros = torch.empty((max(L, 1),), dtype=torch.int64, device=dev) if kind == WT_MATRIX else None
+    perm = torch.empty((n,), dtype=torch.int32, device=dev)
+    srt = torch.empty_like(text) if sorted_text else None
+    if ws is None:
+        ws = torch.empty((max(wt_order_workspace_size(kind, _symtype(text), n, sigma), 1),), dtype=torch.uint8,
+                         device=dev)
+    if kind == WT_TREE:
+        _check(lib().wt_build_order(_ptr(text), _symtype(text), n, int(sigma), _ptr(bv), _ptr(perm), _ptr(srt),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "wt_build_order")
+    else:
+        _check(lib().wm_build_order(_ptr(text), _symtype(text), n, int(sigma), _ptr(bv), _ptr(zeros), _ptr(perm),
+                                    _ptr(srt), _ptr(ws), ws.numel(), _stream(stream)), "wm_build_order")
+    return bv, (zeros[:L] if zeros is not None else None), perm, srt
+
+
 def wt_wm_workspace_size(symtype: int, n: int, sigma: int) -> int:
     out = ctypes.c_size_t(0)
     _check(lib().wt_wm_workspace_size(symtype, int(n), int(sigma), ctypes.byref(out)), "wt_wm_workspace_size")

@@ -15,6 +15,8 @@ struct HostText {
     uint64_t *bv;
     uint64_t *zeros;
     uint64_t *bv2 = nullptr;     // kBoth: the WM's levels (bv holds the WT's)
+    uint32_t *perm = nullptr;    // the stable order after the last level
+    bool order = false;          // perm is wanted (size queries pass no pointer)
 };
 
 struct Plan {
@@ -28,6 +30,7 @@ struct Plan {
     size_t off_ctl = 0, off_texts = 0, off_jobs[2] = {}, off_jobhist[2] = {};
     size_t off_ghist = 0, off_gexcl = 0, off_thist = 0, off_btail = 0, off_bflag = 0, off_bcarry = 0;
     std::vector<size_t> off_buf[2];
+    std::vector<size_t> off_pbuf[2];      // text positions carried through cut rounds (perm)
     std::vector<TextInfo> texts;
     size_t bytes = 0;
 };
@@ -74,6 +77,9 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
         const uint32_t L = levels_of(x.sigma);
         if (kind == WT_TREE && L > (uint32_t)kMaxTreeSigmaLog) return WT_ERR_INVALID_ARG;
         if (both && (L > (uint32_t)kChunk || (x.n > 0 && x.n <= kSmallJob))) return WT_ERR_INVALID_ARG;
+        if (both && x.order) return WT_ERR_INVALID_ARG;
+        if (check_ptrs && x.order && x.n > 0 && (x.perm == nullptr || reinterpret_cast<uintptr_t>(x.perm) % 4))
+            return WT_ERR_INVALID_ARG;
         if (check_ptrs && L > 0) {
             if (x.n > 0 && (x.text == nullptr || x.bv == nullptr)) return WT_ERR_INVALID_ARG;
             if ((kind == WT_MATRIX || both) && x.zeros == nullptr) return WT_ERR_INVALID_ARG;
@@ -85,6 +91,7 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
         ti.text = x.text;
         ti.bv = x.bv;
         ti.bv2 = both ? x.bv2 : nullptr;
+        ti.perm = x.order ? x.perm : nullptr;
         ti.zeros = (kind == WT_MATRIX || both) ? x.zeros : nullptr;
         ti.n = x.n;
         ti.W = (x.n + 63) / 64;
@@ -149,11 +156,15 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
     p.off_bflag = take(sizeof(uint32_t) * (size_t)max_blocks);
     p.off_buf[0].assign(count, 0);
     p.off_buf[1].assign(count, 0);
+    p.off_pbuf[0].assign(count, 0);
+    p.off_pbuf[1].assign(count, 0);
     for (uint32_t i = 0; i < count; ++i) {
         const TextInfo &ti = p.texts[i];
         if (ti.n == 0) continue;
         if (ti.L > kChunk) p.off_buf[0][i] = take(ti.n * width_for_bits(ti.L - kChunk));
         if (ti.L > 2 * kChunk) p.off_buf[1][i] = take(ti.n * width_for_bits(ti.L - 2 * kChunk));
+        if (t[i].order && ti.L > kChunk) p.off_pbuf[0][i] = take(ti.n * sizeof(uint32_t));
+        if (t[i].order && ti.L > 2 * kChunk) p.off_pbuf[1][i] = take(ti.n * sizeof(uint32_t));
     }
     p.bytes = off;
     return WT_OK;
@@ -185,6 +196,8 @@ wt_status prepare(Plan &p, void *d_ws, size_t ws_bytes)
         TextInfo &ti = p.texts[i];
         ti.buf[0] = ti.L > kChunk ? ws + p.off_buf[0][i] : nullptr;
         ti.buf[1] = ti.L > 2 * kChunk ? ws + p.off_buf[1][i] : nullptr;
+        ti.pbuf[0] = ti.perm && ti.L > kChunk ? reinterpret_cast<uint32_t *>(ws + p.off_pbuf[0][i]) : nullptr;
+        ti.pbuf[1] = ti.perm && ti.L > 2 * kChunk ? reinterpret_cast<uint32_t *>(ws + p.off_pbuf[1][i]) : nullptr;
     }
     return WT_OK;
 }
@@ -345,6 +358,61 @@ wt_status wt_wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t 
     wt_status st = make_plan(static_cast<wt_kind>(kBoth), type, &h, 1, true, p);
     if (st != WT_OK) return st;
     return run_plan(static_cast<wt_kind>(kBoth), p, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+wt_status build_order(wt_kind kind, const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                      uint64_t *d_bv, uint64_t *d_zeros, uint32_t *d_perm, void *d_sorted, void *d_ws,
+                      size_t ws_bytes, void *stream)
+{
+    HostText h{d_text, n, sigma, d_bv, d_zeros};
+    h.perm = d_perm;
+    h.order = true;
+    Plan p;
+    wt_status st = make_plan(kind, type, &h, 1, true, p);
+    if (st != WT_OK) return st;
+    if (n == 0) return WT_OK;
+    if (d_perm == nullptr || d_text == nullptr) return WT_ERR_INVALID_ARG;
+    if (d_sorted != nullptr && reinterpret_cast<uintptr_t>(d_sorted) % (uint32_t)type) return WT_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (levels_of(sigma) == 0) {                 // one symbol value: the text order
+        if (ensure_configured() != WT_OK) return WT_ERR_CUDA;
+        return launch_identity_order(d_text, (uint32_t)type, n, d_perm, d_sorted, s) == cudaSuccess ? WT_OK
+                                                                                                    : WT_ERR_CUDA;
+    }
+    st = run_plan(kind, p, d_ws, ws_bytes, s);
+    if (st == WT_OK && d_sorted != nullptr &&
+        launch_gather(d_text, (uint32_t)type, d_perm, n, d_sorted, s) != cudaSuccess)
+        st = WT_ERR_CUDA;
+    return st;
+}
+
+}  // namespace
+
+wt_status wt_order_workspace_size(wt_kind kind, wt_symtype type, uint64_t n, uint64_t sigma, size_t *bytes)
+{
+    if (bytes == nullptr) return WT_ERR_INVALID_ARG;
+    HostText h{nullptr, n, sigma, nullptr, nullptr};
+    h.order = true;
+    Plan p;
+    wt_status st = make_plan(kind, type, &h, 1, false, p, kMinSpb);
+    if (st == WT_OK) *bytes = p.bytes;
+    return st;
+}
+
+wt_status wt_build_order(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv,
+                         uint32_t *d_perm, void *d_sorted, void *d_ws, size_t ws_bytes, void *stream)
+{
+    return build_order(WT_TREE, d_text, type, n, sigma, d_bv, nullptr, d_perm, d_sorted, d_ws, ws_bytes, stream);
+}
+
+wt_status wm_build_order(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv,
+                         uint64_t *d_zeros, uint32_t *d_perm, void *d_sorted, void *d_ws, size_t ws_bytes,
+                         void *stream)
+{
+    return build_order(WT_MATRIX, d_text, type, n, sigma, d_bv, d_zeros, d_perm, d_sorted, d_ws, ws_bytes,
+                       stream);
 }
 
 wt_status wt_sync_status(void *d_ws, void *stream)

@@ -46,6 +46,8 @@ struct TextInfo {
     uint64_t *bv;            // L * W words (the WT's when kind == kBoth)
     uint64_t *bv2;           // kBoth: the WM's L * W words
     uint64_t *zeros;         // WM (and kBoth): L values
+    uint32_t *perm;          // optional: text position of every symbol in the order after the last level
+    uint32_t *pbuf[2];       // perm: text positions in the re-sorted order, round r writes pbuf[r & 1]
     uint64_t n;
     uint64_t W;
     uint64_t sigma;
@@ -94,6 +96,14 @@ struct RoundArgs {
     uint32_t any_cut;        // some job of the round writes a re-sorted text (k_build)
     uint32_t any_plain;      // some job of the round has no cut (k_build_bs)
 };
+
+// sorted[j] = text[perm[j]] for j < n (symbols of width w).
+cudaError_t launch_gather(const void *text, uint32_t w, const uint32_t *perm, uint64_t n, void *sorted,
+                          cudaStream_t s);
+
+// perm[j] = j and sorted = text (texts with a single symbol value, L = 0).
+cudaError_t launch_identity_order(const void *text, uint32_t w, uint64_t n, uint32_t *perm, void *sorted,
+                                  cudaStream_t s);
 
 // Launches one round on the stream.  Returns a CUDA error code.
 cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s);

@@ -8,13 +8,18 @@
 //                                zero-based prefix sum over groups of the same job in
 //                                (class-major, group-minor) order (Alg. 2, Sec. 3.2.1);
 //                                job totals
-//   k_build       (a2-a5)        per tile: fold the histograms to every level and take
-//                                the interval starts (id or bit-reversal order,
-//                                Sec. 3.1 / 5.1); stable one-bit splits of the tile in
-//                                shared memory give, level by level, the bits of each
-//                                interval in text order; ballots pack them into words
-//                                that are copied to their interval starts; the last
-//                                split writes the symbols re-sorted for the next round.
+//   k_build_bs    (a2-a5)        per group of tiles: fold the histograms to every level
+//                                and take the interval starts (id or bit-reversal order,
+//                                Sec. 3.1 / 5.1); the tile as bit planes in shared
+//                                memory; per level, a stable split of the later planes
+//                                (compress to the zero and to the one positions) and a
+//                                copy of each class run to its interval start; in
+//                                rounds that cut, the tile stably sorted by its 8-bit
+//                                class for the next round (and, when asked, the text
+//                                positions in the order after the last level)
+//   k_build_small (a2-a4)        the same for jobs of at most 4096 symbols, one warp each
+//   k_gather / k_identity_order  the sorted text from the stable order
+#include <algorithm>
 #include <cstdio>
 
 #include "wt_internal.h"
@@ -82,7 +87,8 @@ static_assert(kSmallJob == 32 * 32 * kSmallWords, "a small job is one warp's 32 
 
 __device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uint64_t n)
 {
-    return n > 0 && n <= kSmallJob && t.L - kChunk * round <= (uint32_t)kChunk;
+    // texts that want the stable order take the block path, which ranks it
+    return n > 0 && n <= kSmallJob && t.L - kChunk * round <= (uint32_t)kChunk && t.perm == nullptr;
 }
 
 // Lanes whose 8-bit key equals this lane's, among the lanes with ok set: the AND
@@ -922,30 +928,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             __syncthreads();
         }
         // ---- re-sorted symbols for the next round: the tile stably sorted by its
-        //      8-bit class (the counting sort of Alg. 2), each class's run written
+        //      h-bit class (the counting sort of Alg. 2), each class's run written
         //      at its interval start of level h (id order for the WT, reversed for
         //      the WM, Obs. 2); only the low rb - h bits go on.  Ranks: warp w
         //      takes symbols [2048w, 2048w + 2048) in text order, equal classes
         //      within a step are ranked by lane, chunks by a scan over warps.  The
         //      values are staged in sorted order in the (now idle) plane buffers
         //      so that every class run is written with consecutive stores.
-        if (rt.cut != nullptr) {
+        //      When the text wants its stable order, the same ranks place every
+        //      symbol's text position: in the next round's position buffer, or,
+        //      in the last round, in the order after the last level.
+        if (rt.cut != nullptr || t.perm != nullptr) {
             constexpr uint32_t kPer = kBsTile / kWarps;
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             const uint32_t low = (1u << shift) - 1u;
+            const uint32_t cmask = (1u << h) - 1u;       // classes of this round (k_hist counts the same)
             const uint32_t e_end = min(m, warp * kPer + kPer);
             const uint32_t base_h = 1u << h;
             uint16_t *cw = sm.cntw[warp];
             uint8_t *stage8 = reinterpret_cast<uint8_t *>(&sm.plane[0][0][0]);
             uint16_t *stage16 = reinterpret_cast<uint16_t *>(&sm.plane[0][0][0]);
-            const bool staged = rt.cut_w <= 2;        // 32768 values fit the plane buffers
+            const bool staged = rt.cut != nullptr && rt.cut_w <= 2;   // 32768 values fit the plane buffers
+            const uint64_t pos0 = (uint64_t)jb.off + t0;             // round-buffer position of symbol 0
+            const uint32_t *pin = a.round ? t.pbuf[(a.round - 1) & 1] : nullptr;
+            uint32_t *pout = t.perm == nullptr ? nullptr : (rt.cut != nullptr ? t.pbuf[a.round & 1] : t.perm);
             for (uint32_t q = lane; q < kCols; q += 32) cw[q] = 0;
             __syncwarp();
             for (uint32_t e0 = warp * kPer; e0 < e_end; e0 += 32) {
                 const uint32_t e = e0 + lane;
                 const bool ok = e < e_end;
                 const uint32_t v = ok ? load_sym(tile, rt.in_w, e) : 0u;
-                const uint32_t q = ok ? (v >> shift) & 0xffu : 0u;
+                const uint32_t q = ok ? (v >> shift) & cmask : 0u;
                 const uint32_t peers = peers8(q, ok);
                 if (ok && (peers >> lane) == 1u) cw[q] = (uint16_t)(cw[q] + __popc(peers));
                 __syncwarp();
@@ -965,14 +978,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 const uint32_t e = e0 + lane;
                 const bool ok = e < e_end;
                 const uint32_t v = ok ? load_sym(tile, rt.in_w, e) : 0u;
-                const uint32_t q = ok ? (v >> shift) & 0xffu : 0u;
+                const uint32_t q = ok ? (v >> shift) & cmask : 0u;
                 const uint32_t peers = peers8(q, ok);
                 const uint32_t rank = ok ? cw[q] + __popc(peers & lt) : 0u;
                 __syncwarp();
                 if (ok) {
                     if ((peers >> lane) == 1u) cw[q] = (uint16_t)(rank + 1u);
-                    if (!staged) {
-                        store_sym(rt.cut, rt.cut_w, (uint64_t)sm.glo[base_h + q] + rank, v & low);
+                    const uint64_t dst = (uint64_t)sm.glo[base_h + q] + rank;
+                    if (pout != nullptr && dst < t.n) pout[dst] = pin ? pin[pos0 + e] : (uint32_t)(pos0 + e);
+                    if (rt.cut == nullptr) {
+                    } else if (!staged) {
+                        store_sym(rt.cut, rt.cut_w, dst, v & low);
                     } else {
                         const uint32_t pos = sm.loc[base_h + q] + rank;      // place in the sorted tile
                         if (rt.cut_w == 1) stage8[pos] = (uint8_t)(v & low);
@@ -1187,6 +1203,39 @@ cudaError_t configure_kernels()
     e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_build_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
+}
+
+__global__ void k_gather(const void *text, uint32_t w, const uint32_t *perm, uint64_t n, void *sorted)
+{
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x)
+        store_sym(sorted, w, j, load_sym(text, w, perm[j]));
+}
+
+__global__ void k_identity_order(const void *text, uint32_t w, uint64_t n, uint32_t *perm, void *sorted)
+{
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        if (perm) perm[j] = (uint32_t)j;
+        if (sorted) store_sym(sorted, w, j, load_sym(text, w, j));
+    }
+}
+
+cudaError_t launch_gather(const void *text, uint32_t w, const uint32_t *perm, uint64_t n, void *sorted,
+                          cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152ull * 16);
+    k_gather<<<(uint32_t)blocks, 256, 0, s>>>(text, w, perm, n, sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_identity_order(const void *text, uint32_t w, uint64_t n, uint32_t *perm, void *sorted,
+                                  cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152ull * 16);
+    k_identity_order<<<(uint32_t)blocks, 256, 0, s>>>(text, w, n, perm, sorted);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s)
