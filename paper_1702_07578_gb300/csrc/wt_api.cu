@@ -382,10 +382,15 @@ wt_status build_order(wt_kind kind, const void *d_text, wt_symtype type, uint64_
                                                                                                     : WT_ERR_CUDA;
     }
     st = run_plan(kind, p, d_ws, ws_bytes, s);
-    if (st == WT_OK && d_sorted != nullptr &&
-        launch_gather(d_text, (uint32_t)type, d_perm, n, d_sorted, s) != cudaSuccess)
-        st = WT_ERR_CUDA;
-    return st;
+    if (st != WT_OK || d_sorted == nullptr) return st;
+    cudaError_t e;
+    if (p.rounds == 1) {      // runs of equal symbols, lengths from the job's class totals
+        const uint32_t *count = reinterpret_cast<const uint32_t *>(static_cast<uint8_t *>(d_ws) + p.off_jobhist[0]);
+        e = launch_fill_runs(count, levels_of(sigma), kind == WT_MATRIX, n, d_sorted, (uint32_t)type, s);
+    } else {
+        e = launch_gather(d_text, (uint32_t)type, d_perm, n, d_sorted, s);
+    }
+    return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 
 }  // namespace

@@ -101,6 +101,11 @@ struct RoundArgs {
 cudaError_t launch_gather(const void *text, uint32_t w, const uint32_t *perm, uint64_t n, void *sorted,
                           cudaStream_t s);
 
+// sorted for a text built in one round (L <= 8) from its class totals: count[c]
+// copies of c, runs in id order (WT) or reversed-code order (WM).
+cudaError_t launch_fill_runs(const uint32_t *count, uint32_t L, bool matrix, uint64_t n, void *sorted, uint32_t w,
+                             cudaStream_t s);
+
 // perm[j] = j and sorted = text (texts with a single symbol value, L = 0).
 cudaError_t launch_identity_order(const void *text, uint32_t w, uint64_t n, uint32_t *perm, void *sorted,
                                   cudaStream_t s);

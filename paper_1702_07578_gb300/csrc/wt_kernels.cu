@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         __syncthreads();
         // per level (one warp each): class starts in tile order (reversed
         // prefixes, Obs. 2) and destination words of every class
-        if (warp == h && rt.cut != nullptr) {       // class starts after the last split (cut)
+        if (warp == h && (rt.cut != nullptr || t.perm != nullptr)) {   // class starts after the last split
             const uint32_t base = 1u << h;
             warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
                           [&](uint32_t i) { return rev_bits(i, h); },
@@ -949,20 +949,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             uint8_t *stage8 = reinterpret_cast<uint8_t *>(&sm.plane[0][0][0]);
             uint16_t *stage16 = reinterpret_cast<uint16_t *>(&sm.plane[0][0][0]);
             const bool staged = rt.cut != nullptr && rt.cut_w <= 2;   // 32768 values fit the plane buffers
+            // last round: the 15-bit tile offsets of the symbols are staged in sorted
+            // order instead (64 KB), and every class run of positions is written with
+            // consecutive stores
+            const bool pstaged = t.perm != nullptr && rt.cut == nullptr;
             const uint64_t pos0 = (uint64_t)jb.off + t0;             // round-buffer position of symbol 0
             const uint32_t *pin = a.round ? t.pbuf[(a.round - 1) & 1] : nullptr;
             uint32_t *pout = t.perm == nullptr ? nullptr : (rt.cut != nullptr ? t.pbuf[a.round & 1] : t.perm);
-            for (uint32_t q = lane; q < kCols; q += 32) cw[q] = 0;
+            // 32-bit per-warp counters for the atomics (16 warps x 256 words = 16 KB)
+            // in the second half of the plane buffers, idle between the level loop
+            // and the staging below
+            uint32_t *cwc = reinterpret_cast<uint32_t *>(&sm.plane[1][0][0]) + warp * kCols;
+            for (uint32_t q = lane; q < kCols; q += 32) cwc[q] = 0;
             __syncwarp();
-            for (uint32_t e0 = warp * kPer; e0 < e_end; e0 += 32) {
-                const uint32_t e = e0 + lane;
-                const bool ok = e < e_end;
-                const uint32_t v = ok ? load_sym(tile, rt.in_w, e) : 0u;
-                const uint32_t q = ok ? (v >> shift) & cmask : 0u;
-                const uint32_t peers = peers8(q, ok);
-                if (ok && (peers >> lane) == 1u) cw[q] = (uint16_t)(cw[q] + __popc(peers));
-                __syncwarp();
+            // symbols in chunks of 8 steps of 32: the 8 loads of a lane are issued
+            // together, so a chunk waits for memory once
+            constexpr uint32_t kSteps = 8;
+            static_assert(kPer % (32 * kSteps) == 0, "whole chunks per warp");
+            for (uint32_t c0 = warp * kPer; c0 < e_end; c0 += 32 * kSteps) {
+                uint32_t vs[kSteps];
+#pragma unroll
+                for (uint32_t k = 0; k < kSteps; ++k) {
+                    const uint32_t e = c0 + 32 * k + lane;
+                    vs[k] = e < e_end ? load_sym(tile, rt.in_w, e) : 0u;
+                }
+                // counts only (the ranks below are taken stably): one shared
+                // atomic per symbol on this warp's own row
+#pragma unroll
+                for (uint32_t k = 0; k < kSteps; ++k)
+                    if (c0 + 32 * k + lane < e_end) atomicAdd(&cwc[((vs[k] >> shift) & cmask)], 1u);
             }
+            __syncwarp();
+            for (uint32_t q = lane; q < kCols; q += 32) cw[q] = (uint16_t)cwc[q];
             __syncthreads();
             for (uint32_t q = tid; q < kCols; q += kThreads) {
                 uint32_t run = 0;
@@ -974,28 +992,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             }
             __syncthreads();
             const uint32_t lt = lanemask_lt();
-            for (uint32_t e0 = warp * kPer; e0 < e_end; e0 += 32) {
-                const uint32_t e = e0 + lane;
-                const bool ok = e < e_end;
-                const uint32_t v = ok ? load_sym(tile, rt.in_w, e) : 0u;
-                const uint32_t q = ok ? (v >> shift) & cmask : 0u;
-                const uint32_t peers = peers8(q, ok);
-                const uint32_t rank = ok ? cw[q] + __popc(peers & lt) : 0u;
-                __syncwarp();
-                if (ok) {
-                    if ((peers >> lane) == 1u) cw[q] = (uint16_t)(rank + 1u);
-                    const uint64_t dst = (uint64_t)sm.glo[base_h + q] + rank;
-                    if (pout != nullptr && dst < t.n) pout[dst] = pin ? pin[pos0 + e] : (uint32_t)(pos0 + e);
-                    if (rt.cut == nullptr) {
-                    } else if (!staged) {
-                        store_sym(rt.cut, rt.cut_w, dst, v & low);
-                    } else {
-                        const uint32_t pos = sm.loc[base_h + q] + rank;      // place in the sorted tile
-                        if (rt.cut_w == 1) stage8[pos] = (uint8_t)(v & low);
-                        else stage16[pos] = (uint16_t)(v & low);
-                    }
+            for (uint32_t c0 = warp * kPer; c0 < e_end; c0 += 32 * kSteps) {
+                uint32_t vs[kSteps];
+#pragma unroll
+                for (uint32_t k = 0; k < kSteps; ++k) {
+                    const uint32_t e = c0 + 32 * k + lane;
+                    vs[k] = e < e_end ? load_sym(tile, rt.in_w, e) : 0u;
                 }
-                __syncwarp();
+#pragma unroll
+                for (uint32_t k = 0; k < kSteps; ++k) {
+                    const uint32_t e = c0 + 32 * k + lane;
+                    const bool ok = e < e_end;
+                    const uint32_t v = vs[k];
+                    const uint32_t q = ok ? (v >> shift) & cmask : 0u;
+                    const uint32_t peers = peers8(q, ok);
+                    const uint32_t rank = ok ? cw[q] + __popc(peers & lt) : 0u;
+                    __syncwarp();
+                    if (ok) {
+                        if ((peers >> lane) == 1u) cw[q] = (uint16_t)(rank + 1u);
+                        const uint64_t dst = (uint64_t)sm.glo[base_h + q] + rank;
+                        if (pstaged)
+                            stage16[sm.loc[base_h + q] + rank] = (uint16_t)e;
+                        else if (pout != nullptr && dst < t.n)
+                            pout[dst] = pin ? pin[pos0 + e] : (uint32_t)(pos0 + e);
+                        if (rt.cut == nullptr) {
+                        } else if (!staged) {
+                            store_sym(rt.cut, rt.cut_w, dst, v & low);
+                        } else {
+                            const uint32_t pos = sm.loc[base_h + q] + rank;   // place in the sorted tile
+                            if (rt.cut_w == 1) stage8[pos] = (uint8_t)(v & low);
+                            else stage16[pos] = (uint16_t)(v & low);
+                        }
+                    }
+                    __syncwarp();
+                }
             }
             __syncthreads();
             if (staged) {                               // class runs, one warp per class
@@ -1004,6 +1034,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     const uint64_t dst = sm.glo[base_h + q];
                     for (uint32_t i = lane; i < c; i += 32)
                         store_sym(rt.cut, rt.cut_w, dst + i, rt.cut_w == 1 ? stage8[src + i] : stage16[src + i]);
+                }
+                __syncthreads();
+            }
+            if (pstaged) {                              // class runs of text positions
+                for (uint32_t q = warp; q < base_h; q += kWarps) {
+                    const uint32_t c = sm.cnt[base_h + q], src = sm.loc[base_h + q];
+                    const uint64_t dst = sm.glo[base_h + q];
+                    for (uint32_t i = lane; i < c; i += 32) {
+                        const uint32_t e = stage16[src + i];
+                        if (dst + i < t.n) pout[dst + i] = pin ? pin[pos0 + e] : (uint32_t)(pos0 + e);
+                    }
                 }
                 __syncthreads();
             }
@@ -1218,6 +1259,55 @@ __global__ void k_identity_order(const void *text, uint32_t w, uint64_t n, uint3
         if (perm) perm[j] = (uint32_t)j;
         if (sorted) store_sym(sorted, w, j, load_sym(text, w, j));
     }
+}
+
+// A text built in one round: its symbols after the last level are runs of equal
+// symbols, c repeated count[c] times, the runs in id order (WT) or in the order of
+// the reversed L-bit codes (WM).  Each block fills one contiguous chunk of the
+// output; a thread keeps the run it is in and searches again (binary search over
+// the run starts) only when it passes the run's end.
+__global__ void __launch_bounds__(256) k_fill_runs(const uint32_t *count, uint32_t L, uint32_t matrix, uint64_t n,
+                                                   void *sorted, uint32_t w)
+{
+    __shared__ uint32_t start[kCols + 1];
+    __shared__ uint32_t sym[kCols];
+    const uint32_t nc = 1u << L;
+    if (threadIdx.x < 32) {
+        const uint32_t tot = warp_scan_256(nc, [&](uint32_t c) { return count[c]; },
+                                           [&](uint32_t i) { return matrix ? rev_bits(i, L) : i; },
+                                           [&](uint32_t c, uint32_t v) {
+                                               const uint32_t i = matrix ? rev_bits(c, L) : c;   // c's run
+                                               start[i] = v;
+                                               sym[i] = c;
+                                           });
+        if (threadIdx.x == 0) start[nc] = tot;
+    }
+    __syncthreads();
+    const uint64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t j0 = (uint64_t)blockIdx.x * chunk, j1 = min(n, j0 + chunk);
+    uint64_t end = 0;                                // end of the current run (0: none yet)
+    uint32_t cur = 0;
+    for (uint64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        if (j >= end) {
+            uint32_t lo = 0, hi = nc;                // last run starting at or before j
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (start[mid] <= j) lo = mid; else hi = mid;
+            }
+            cur = sym[lo];
+            end = start[lo + 1];
+        }
+        store_sym(sorted, w, j, cur);
+    }
+}
+
+cudaError_t launch_fill_runs(const uint32_t *count, uint32_t L, bool matrix, uint64_t n, void *sorted, uint32_t w,
+                             cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152ull * 16);
+    k_fill_runs<<<(uint32_t)blocks, 256, 0, s>>>(count, L, matrix ? 1u : 0u, n, sorted, w);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const void *text, uint32_t w, const uint32_t *perm, uint64_t n, void *sorted,
