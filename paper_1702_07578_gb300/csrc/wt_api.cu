@@ -248,6 +248,7 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
             const TextInfo &ti = p.texts[i];
             if (ti.nslots[r] == 0) continue;
             if (ti.L - kChunk * r > (uint32_t)kChunk) a.any_cut = 1; else a.any_plain = 1;
+            if (ti.perm != nullptr) a.any_order = 1;
         }
         if (launch_round(a, p.width[r], s) != cudaSuccess) return WT_ERR_CUDA;
     }

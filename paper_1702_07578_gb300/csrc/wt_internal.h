@@ -93,8 +93,9 @@ struct RoundArgs {
     uint32_t gelems;         // symbols per group in this round
     uint32_t groups_ub;      // grid bound for per-group kernels
     uint32_t blocks_ub;      // grid bound for per-block kernels
-    uint32_t any_cut;        // some job of the round writes a re-sorted text (k_build)
-    uint32_t any_plain;      // some job of the round has no cut (k_build_bs)
+    uint32_t any_cut;        // some job of the round writes a re-sorted text
+    uint32_t any_plain;      // some job of the round has no cut (its text's last round)
+    uint32_t any_order;      // some text of the round wants its stable order (perm)
 };
 
 // sorted[j] = text[perm[j]] for j < n (symbols of width w).

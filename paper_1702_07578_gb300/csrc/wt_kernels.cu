@@ -684,6 +684,10 @@ __device__ __forceinline__ void store_planes(uint32_t x[8], uint32_t rb, uint32_
 
 }  // namespace
 
+// BOTH: kind kBoth (two sets of destinations).  CUT: the round runs the cut pass
+// (some job cuts, or some text wants its stable order); the plain build of texts
+// with sigma <= 256 is the instantiation without either.
+template <bool BOTH, bool CUT>
 __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -700,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const uint32_t shift = rb - h;                   // > 0 in rounds with a cut
     const uint32_t gi = g - jb.g0;
     const bool matrix = a.kind == WT_MATRIX;
-    const bool both = a.kind == kBoth;
+    constexpr bool both = BOTH;
 
     // job totals -> class totals and interval starts of every level (fold,
     // Alg. 1; zero-based prefix sums in id or pi_l order, Sec. 3.1 / 5.1)
@@ -777,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         __syncthreads();
         // per level (one warp each): class starts in tile order (reversed
         // prefixes, Obs. 2) and destination words of every class
-        if (warp == h && (rt.cut != nullptr || t.perm != nullptr)) {   // class starts after the last split
+        if (CUT && warp == h && (rt.cut != nullptr || t.perm != nullptr)) {   // class starts after the last split
             const uint32_t base = 1u << h;
             warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
                           [&](uint32_t i) { return rev_bits(i, h); },
@@ -938,7 +942,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         //      When the text wants its stable order, the same ranks place every
         //      symbol's text position: in the next round's position buffer, or,
         //      in the last round, in the order after the last level.
-        if (rt.cut != nullptr || t.perm != nullptr) {
+        if (CUT && (rt.cut != nullptr || t.perm != nullptr)) {
             constexpr uint32_t kPer = kBsTile / kWarps;
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             const uint32_t low = (1u << shift) - 1u;
@@ -1243,7 +1247,11 @@ cudaError_t configure_kernels()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_build_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
+    for (auto k : {k_build_bs<false, false>, k_build_bs<false, true>, k_build_bs<true, false>}) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 __global__ void k_gather(const void *text, uint32_t w, const uint32_t *perm, uint64_t n, void *sorted)
@@ -1355,7 +1363,12 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     k_blockscan<<<1, 256, 0, s>>>(a);
     k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
     if (prof) { profile_mark(2, false, s); profile_mark(0, true, s); }
-    k_build_bs<<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    if (a.kind == kBoth)
+        k_build_bs<true, false><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    else if (a.any_cut || a.any_order)
+        k_build_bs<false, true><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    else
+        k_build_bs<false, false><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
     if (a.any_plain && a.kind != kBoth)           // kBoth has no small jobs
         k_build_small<<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
                         sizeof(SmallSmem) * kSmallWarps, s>>>(a);
