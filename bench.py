@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (profiles/k_build_bs_bytes_n2e28_full.md)
-    "30195a6b4b016f0a71609e38b4ef042a375ef77a0daf3a77af9d3ec3ea8df858": {"dram_bytes": 344495360 + 222899200,
+    "38a08768ec7561a6039c45022c786a71012f0ae62d811a067ce90ad215cd7400": {"dram_bytes": 345465344 + 222891520,
                                                                          "n": 1 << 28},
 }
 
