@@ -14,9 +14,9 @@ from tests.gpu_util import first_diff, gpu_wm, gpu_wt
 
 pytestmark = pytest.mark.gpu
 
-TILE8 = 512 * 32          # u8 tile (symbols)
-GROUP8 = TILE8 * 4        # symbols per build block for u8
-TILE16 = 512 * 16
+TILE = 512 * 2 * 32       # symbols per tile of the split kernel (512 threads x 2 words x 32)
+GROUP = 2 * TILE          # symbols per build block (default)
+SMALL = 4096              # largest job built by one warp
 
 
 def _check(T, sigma):
@@ -39,8 +39,8 @@ def test_worked_example():
     _check(T, 8)
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 63, 64, 65, 127, 1000, TILE8 - 1, TILE8, TILE8 + 1,
-                               GROUP8 - 1, GROUP8, GROUP8 + 1, 3 * GROUP8 + 12345])
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 1000, SMALL - 1, SMALL, SMALL + 1,
+                               TILE - 1, TILE, TILE + 1, GROUP - 1, GROUP, GROUP + 1, 3 * GROUP + 12345])
 def test_lengths_u8_sigma256(n):
     T = synth.uniform_text(n, 256, 100 + n, np.uint8)
     _check(T, 256)
@@ -77,7 +77,7 @@ def test_matrix_up_to_32_levels():
 
 @pytest.mark.parametrize("shape", ["constant", "sorted", "reverse", "alternating", "zeros"])
 def test_structured_texts(shape):
-    n = 2 * GROUP8 + 777
+    n = 2 * GROUP + 777
     if shape == "constant":
         T = np.full(n, 201, np.uint8)
     elif shape == "zeros":
@@ -134,3 +134,36 @@ def test_argument_errors_are_immediate():
     small = torch.empty(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(wtg.WtError):
         wtg.wt_build(t, 256, ws=small)        # workspace too small
+
+
+def _random_text(rng, n, sigma, dtype):
+    kind = int(rng.integers(0, 4))
+    if kind == 0:
+        return synth.uniform_text(n, sigma, int(rng.integers(1, 1 << 30)), dtype)
+    if kind == 1:
+        return synth.zipf_text(n, sigma, float(rng.uniform(0.5, 1.5)), int(rng.integers(1, 1 << 30)), dtype)
+    if kind == 2:                                    # long runs of equal symbols
+        runs = rng.integers(1, 5000, size=max(1, n // 100))
+        vals = rng.integers(0, sigma, size=runs.size)
+        return np.resize(np.repeat(vals, runs), n).astype(dtype)
+    return (np.arange(n, dtype=np.int64) * int(rng.integers(1, 97)) % sigma).astype(dtype)   # periodic
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_shapes(seed):
+    """Seeded sweep: lengths around tile and group edges and in between, alphabets
+    from 2 to 2^20 (one to three rounds), every storage width that holds them,
+    uniform / Zipf / long runs / periodic texts."""
+    rng = np.random.default_rng(9000 + seed)
+    edges = [SMALL, TILE, GROUP, 2 * GROUP, 5 * TILE]
+    for _ in range(5):
+        if rng.random() < 0.5:
+            n = int(rng.choice(edges)) + int(rng.integers(-3, 4))
+        else:
+            n = int(rng.integers(0, 400000))
+        sigma = int(rng.choice([2, 3, 7, 64, 200, 256, 257, 1000, 4096, 40000, 65536, 1 << 18, 1 << 20]))
+        widths = [np.uint8, np.uint16, np.uint32]
+        ok = [w for w in widths if sigma <= (1 << (8 * np.dtype(w).itemsize))]
+        dtype = ok[int(rng.integers(0, len(ok)))]
+        T = _random_text(rng, max(n, 0), sigma, dtype)
+        _check(T, sigma)
