@@ -17,6 +17,8 @@ uint64, level-major, bit j of a level at bit ``j & 63`` of word ``j >> 6``):
 ``wt2wm(T, sigma, l, i)``   Lemma 3: WT position -> WM position (``lemma3.py``, numpy)
 ``stable_order(T, sigma, kind)``  the order after the last level, as a permutation and
                             as the sorted text (``order.py``, numpy)
+``merge(kind, L, slices)``  merge of the partial WT/WM of consecutive slices, Sec. 3.3
+                            (``merge.py``, numpy)
 """
 from __future__ import annotations
 
@@ -149,3 +151,4 @@ def bits_string(bv_level, n):
 
 from .lemma3 import wt2wm, wt2wm_tables  # noqa: E402,F401
 from .order import stable_order  # noqa: E402,F401
+from .merge import merge  # noqa: E402,F401
