@@ -645,6 +645,62 @@ def run_served(args):
 
 
 # ---------------------------------------------------------------------------
+# large: a text beyond 2^32 symbols, built in slices and merged (Sec. 3.3)
+
+def run_large(args):
+    """Per step: wt_build_large + wm_build_large of n = 2^32 + 2^30 resident Zipf bytes."""
+    import torch
+    import paper_1702_07578_gb300 as wtg
+    import synth
+
+    rank, local, world, pg = dist()
+    torch.cuda.set_device(local)
+    n = (1 << 32) + (1 << 30) if args.n_log2 is None else (1 << args.n_log2)
+    T = synth.zipf_text(n, 256, 1.0, synth.SEED_BASE + 1, np.uint8)
+    text = torch.from_numpy(T).cuda()
+    del T
+    L = 8
+    W = wtg.wt_words_per_level(n)
+    bv_t = torch.empty((L, W), dtype=torch.int64, device="cuda")
+    bv_m = torch.empty((L, W), dtype=torch.int64, device="cuda")
+    z = torch.empty((L,), dtype=torch.int64, device="cuda")
+    ws = torch.empty((max(wtg.wt_large_workspace_size(k, 1, n, 256, 0) for k in (0, 1)),), dtype=torch.uint8,
+                     device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        wtg.build_large(wtg.WT_TREE, text, 256, bv=bv_t, ws=ws, stream=stream)
+        wtg.build_large(wtg.WT_MATRIX, text, 256, bv=bv_m, zeros=z, ws=ws, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    wtg.wt_sync_status(ws)
+    torch.cuda.synchronize()
+    barrier(pg)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
+    assert int(z.sum().item()) > 0
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "input symbols/s, WT+WM construction of a text beyond 2^32 symbols (slices + merge)",
+        "value": world * 2 * n / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"WT+WM, n={n} uint8, sigma=256, Zipf(1.0) over a seeded permutation",
+                   "n": n, "slices": -(-n // (1 << 31)), "slice": 1 << 31,
+                   "l2": "inputs larger than L2 (no flush)"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # order: the stable order after the last level as a by-product of the builds
 
 def run_order(args):
@@ -785,7 +841,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bytes",
-                    choices=["bytes", "small", "large_alphabet", "batched", "served", "queries", "order"])
+                    choices=["bytes", "small", "large_alphabet", "batched", "served", "queries", "order",
+                             "large"])
     ap.add_argument("--queries", type=int, default=1 << 24)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
@@ -812,6 +869,8 @@ def main():
         return run_queries(args)
     if args.workload == "order":
         return run_order(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_ours(args)
 
 

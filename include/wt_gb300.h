@@ -93,6 +93,25 @@ wt_status wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sig
  * this workspace during the last build on it (WT_OK if none), then clear it. */
 wt_status wt_sync_status(void *d_ws, void *stream);
 
+/* ---- texts of any length: domain decomposition (Sec. 3.3) ---------------------
+ * For texts of 2^32 symbols or more (up to 2^40), which the builds above do not
+ * take, and for sigma <= 256.  The text is cut into consecutive slices of `slice`
+ * symbols (0: 2^31; at most 2^32 - 1, at most 2^16 slices); each slice is built
+ * on its own (wt_build / wm_build) into partial levels in the workspace, and the
+ * partial levels are merged: merged level l is, prefix by prefix in id order (WT)
+ * or bit-reversal order (WM), the slices' intervals of that prefix in slice order,
+ * placed by a zero-based prefix sum of their sizes; Z[l] is the sum of the slices'.
+ * The output is bit-identical to wt_build / wm_build of the whole text, with the
+ * same layout (W = ceil(n / 64) words per level, now 64-bit counts).  The
+ * workspace (wt_large_workspace_size) holds one slice build's workspace, the
+ * partial levels (about L * n / 8 bytes) and small tables.  wt_sync_status on
+ * the workspace returns the first device-detected error of any slice. */
+wt_status wt_large_workspace_size(wt_kind kind, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t slice,
+                                  size_t *bytes);
+wt_status wt_build_large(wt_kind kind, const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                         uint64_t slice, uint64_t *d_bv, uint64_t *d_zeros, void *d_ws, size_t ws_bytes,
+                         void *stream);
+
 /* ---- the stable order as a by-product ----------------------------------------
  * The splits that build the levels leave the symbols, after the last level, in
  * one stable order (Obs. 1 and Obs. 2 one level past the last): for the WT, T

@@ -124,6 +124,34 @@ def wm_build(text, sigma: int, bv=None, zeros=None, ws=None, stream=None):
     return bv, zeros[:wt_levels(sigma)]
 
 
+def wt_large_workspace_size(kind: int, symtype: int, n: int, sigma: int, slice_len: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().wt_large_workspace_size(kind, symtype, int(n), int(sigma), int(slice_len), ctypes.byref(out)),
+           "wt_large_workspace_size")
+    return out.value
+
+
+def build_large(kind: int, text, sigma: int, slice_len: int = 0, bv=None, zeros=None, ws=None, stream=None):
+    """WT or WM of a device text of any length (slices built separately, then merged);
+    returns (bit vectors, Z or None)."""
+    torch = _torch()
+    if not text.is_cuda or not text.is_contiguous():
+        raise ValueError("text must be a contiguous CUDA tensor")
+    n = text.numel()
+    L = wt_levels(sigma)
+    dev = text.device
+    if bv is None:
+        bv = torch.empty((L, wt_words_per_level(n)), dtype=torch.int64, device=dev)
+    if kind == WT_MATRIX and zeros is None:
+        zeros = torch.empty((max(L, 1),), dtype=torch.int64, device=dev)
+    if ws is None:
+        ws = torch.empty((max(wt_large_workspace_size(kind, _symtype(text), n, sigma, slice_len), 1),),
+                         dtype=torch.uint8, device=dev)
+    _check(lib().wt_build_large(kind, _ptr(text), _symtype(text), n, int(sigma), int(slice_len), _ptr(bv),
+                                _ptr(zeros), _ptr(ws), ws.numel(), _stream(stream)), "wt_build_large")
+    return bv, (zeros[:L] if zeros is not None else None)
+
+
 def wt_order_workspace_size(kind: int, symtype: int, n: int, sigma: int) -> int:
     out = ctypes.c_size_t(0)
     _check(lib().wt_order_workspace_size(kind, symtype, int(n), int(sigma), ctypes.byref(out)),

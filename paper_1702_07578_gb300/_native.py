@@ -164,6 +164,10 @@ SIGNATURES = {
                            _C.c_void_p, _C.c_void_p, _C.c_uint32, _C.c_void_p, _C.c_void_p]),
     "wt_select": (_C.c_int, [_C.c_int, _C.c_void_p, _C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64,
                              _C.c_void_p, _C.c_void_p, _C.c_uint32, _C.c_void_p, _C.c_void_p]),
+    "wt_large_workspace_size": (_C.c_int, [_C.c_int, _C.c_int, _C.c_uint64, _C.c_uint64, _C.c_uint64,
+                                           _C.POINTER(_C.c_size_t)]),
+    "wt_build_large": (_C.c_int, [_C.c_int, _C.c_void_p, _C.c_int, _C.c_uint64, _C.c_uint64, _C.c_uint64,
+                                  _C.c_void_p, _C.c_void_p, _C.c_void_p, _C.c_size_t, _C.c_void_p]),
     "wt_order_workspace_size": (_C.c_int, [_C.c_int, _C.c_int, _C.c_uint64, _C.c_uint64,
                                            _C.POINTER(_C.c_size_t)]),
     "wt_build_order": (_C.c_int, [_C.c_void_p, _C.c_int, _C.c_uint64, _C.c_uint64, _C.c_void_p, _C.c_void_p,
