@@ -421,6 +421,37 @@ wt_status wm_build_order(const void *d_text, wt_symtype type, uint64_t n, uint64
                        stream);
 }
 
+}  // extern "C"
+
+namespace wtg {
+
+// One text of at most 8 levels built into d_bv (and d_zeros); its class totals
+// (256 u32) are copied to d_counts from the build's job totals, or counted by a
+// separate pass when the text is a small job (which has no totals).
+wt_status build_with_counts(wt_kind kind, const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                            uint64_t *d_bv, uint64_t *d_zeros, void *d_ws, size_t ws_bytes, uint32_t *d_counts,
+                            cudaStream_t s)
+{
+    HostText h{d_text, n, sigma, d_bv, d_zeros};
+    Plan p;
+    wt_status st = make_plan(kind, type, &h, 1, true, p);
+    if (st != WT_OK) return st;
+    if (p.rounds != 1) return WT_ERR_INVALID_ARG;
+    st = run_plan(kind, p, d_ws, ws_bytes, s);
+    if (st != WT_OK) return st;
+    if (n > kSmallJob) {
+        const void *tot = static_cast<uint8_t *>(d_ws) + p.off_jobhist[0];
+        return cudaMemcpyAsync(d_counts, tot, sizeof(uint32_t) * kCols, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+                   ? WT_OK
+                   : WT_ERR_CUDA;
+    }
+    return launch_class_counts(d_text, (uint32_t)type, n, d_counts, s) == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+}  // namespace wtg
+
+extern "C" {
+
 wt_status wt_sync_status(void *d_ws, void *stream)
 {
     if (d_ws == nullptr) return WT_ERR_INVALID_ARG;

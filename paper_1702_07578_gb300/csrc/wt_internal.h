@@ -107,6 +107,15 @@ cudaError_t launch_gather(const void *text, uint32_t w, const uint32_t *perm, ui
 cudaError_t launch_fill_runs(const uint32_t *count, uint32_t L, bool matrix, uint64_t n, void *sorted, uint32_t w,
                              cudaStream_t s);
 
+// counts[c] += number of symbols with low 8 bits c (zeroed by the caller).
+cudaError_t launch_class_counts(const void *text, uint32_t w, uint64_t n, uint32_t *counts, cudaStream_t s);
+
+// A one-round build (L <= 8) of one text that also leaves its 256 class totals in
+// d_counts (device).  Used by the builds of texts of any length.
+wt_status build_with_counts(wt_kind kind, const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma,
+                            uint64_t *d_bv, uint64_t *d_zeros, void *d_ws, size_t ws_bytes, uint32_t *d_counts,
+                            cudaStream_t s);
+
 // perm[j] = j and sorted = text (texts with a single symbol value, L = 0).
 cudaError_t launch_identity_order(const void *text, uint32_t w, uint64_t n, uint32_t *perm, void *sorted,
                                   cudaStream_t s);

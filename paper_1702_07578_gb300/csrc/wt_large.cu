@@ -73,7 +73,7 @@ wt_status large_plan(wt_kind kind, wt_symtype type, uint64_t n, uint64_t sigma, 
     return WT_OK;
 }
 
-// class counts of one slice (all of its 8-bit codes), one shared histogram per block
+// class counts of a text (its symbols' low 8 bits), one shared histogram per block
 __global__ void __launch_bounds__(256) k_slice_counts(const void *text, uint32_t w, uint64_t n, uint32_t *counts)
 {
     __shared__ uint32_t h[kCols];
@@ -90,6 +90,17 @@ __global__ void __launch_bounds__(256) k_slice_counts(const void *text, uint32_t
     __syncthreads();
     if (h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
 }
+
+}  // namespace
+
+cudaError_t launch_class_counts(const void *text, uint32_t w, uint64_t n, uint32_t *counts, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_slice_counts<<<(uint32_t)((n + 65535) / 65536), 256, 0, s>>>(text, w, n, counts);
+    return cudaGetLastError();
+}
+
+namespace {
 
 __device__ __forceinline__ uint32_t rev_l(uint32_t q, uint32_t l) { return l ? (__brev(q) >> (32u - l)) : 0u; }
 
@@ -166,15 +177,23 @@ __global__ void __launch_bounds__(256) k_merge(const Run *runs, uint32_t R, cons
                                                uint32_t L, uint32_t l, uint64_t slice, uint64_t n, uint64_t *out,
                                                uint64_t W)
 {
+    __shared__ uint32_t first;
     const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (threadIdx.x == 0) {                           // last run starting at or before the block's first bit
+        const uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x * 64;
+        uint32_t lo = 0, hi = R;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (runs[mid].dst <= p0) lo = mid; else hi = mid;
+        }
+        first = lo;
+    }
+    __syncthreads();
     if (w >= W) return;
     uint64_t pos = w * 64;
     const uint64_t end = min(n, pos + 64);
-    uint32_t lo = 0, hi = R;                          // last run starting at or before pos
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (runs[mid].dst <= pos) lo = mid; else hi = mid;
-    }
+    uint32_t lo = first;                              // forward to the run holding pos
+    while (lo + 1 < R && runs[lo + 1].dst <= pos) ++lo;
     uint64_t word = 0;
     for (uint32_t r = lo; pos < end && r < R; ++r) {
         const Run x = runs[r];
@@ -265,12 +284,10 @@ wt_status wt_build_large(wt_kind kind, const void *d_text, wt_symtype type, uint
         const uint64_t nc = n - c * p.slice < p.slice ? n - c * p.slice : p.slice;
         const uint8_t *tc = static_cast<const uint8_t *>(d_text) + c * p.slice * w;
         uint64_t *bc = partial + c * p.L * p.Ws;
-        st = matrix ? wm_build(tc, type, nc, sigma, bc, zp + c * p.L, sws, p.slice_ws, stream)
-                    : wt_build(tc, type, nc, sigma, bc, sws, p.slice_ws, stream);
+        st = build_with_counts(kind, tc, type, nc, sigma, bc, matrix ? zp + c * p.L : nullptr, sws, p.slice_ws,
+                               counts + c * kCols, s);
         if (st != WT_OK) return st;
         k_keep_status<<<1, 1, 0, s>>>(ctl_status, saved, 0u);
-        const uint32_t blocks = (uint32_t)((nc + 65535) / 65536);
-        k_slice_counts<<<blocks, 256, 0, s>>>(tc, w, nc, counts + c * kCols);
     }
     const uint64_t W = (n + 63) / 64;
     for (uint32_t l = 0; l < p.L; ++l) {
