@@ -362,7 +362,7 @@ wt_status wt_wt2wm(const void *d_map, uint64_t n, uint64_t sigma, const uint32_t
  * its own stream before and after each kernel it launches (the work itself is
  * unchanged).  wt_profile_read() waits for the recorded events and returns the
  * summed milliseconds and launch counts per kernel family since the last
- * reset:  [0] split/scatter (k_build)   [1] histogram (k_hist)
+ * reset:  [0] split/scatter (k_build_bs, k_build_small)   [1] histogram (k_hist)
  *         [2] segmented scan (3 kernels) [3] job lists (2-3 kernels).
  * Not thread-safe with concurrent builds; meant for benchmarks. */
 typedef struct {
