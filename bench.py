@@ -451,6 +451,17 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # batched workload: one graph replay per kind vs one wt_build / wm_build per text
 
+def batched_roofline(texts, sigmas, ms):
+    """Whole-step roofline of the batched build: per text one read (2 B per uint16
+    symbol) and L_i bits written per symbol, for the WT and the WM."""
+    import paper_1702_07578_gb300 as wtg
+    peak, peak_kind = peaks()
+    nbytes = 2 * sum(t.size * (t.dtype.itemsize + wtg.wt_levels(s) / 8.0) for t, s in zip(texts, sigmas))
+    achieved = nbytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "whole step (all kernels of both graph replays)", "peak_kind": peak_kind}
+
+
 def run_batched(args):
     import torch
     import paper_1702_07578_gb300 as wtg
@@ -534,6 +545,7 @@ def run_batched(args):
         "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
                   "launch": f"{2 * count} wt_build/wm_build calls per step"},
         "speedup_vs_plain": value / plain_value,
+        "roofline": batched_roofline(texts_h, sigmas, ms),
     }
     print(json.dumps(line), flush=True)
     return 0
