@@ -1061,8 +1061,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 
 // ---------------------------------------------------------------------------
 // Small jobs (at most kSmallJob symbols, last round of their text): one warp
-// builds a whole job with the same bit-sliced splits as k_build_bs, lane i
-// owning word i (symbols 32i .. 32i + 31), with no block-wide barrier.  Wavelet
+// builds a whole job with the same bit-sliced splits as k_build_bs, with no
+// block-wide barrier.  Lane i owns words i, 32 + i, 64 + i, 96 + i (row j holds
+// words 32j .. 32j + 31), and a job runs only the rows its symbols fill, so a job
+// of a few hundred symbols costs one row.  Wavelet
 // tree rounds >= 1 split every text into one job per prefix (Sec. 2: the
 // independent subtrees), most of them small.
 
@@ -1083,7 +1085,7 @@ struct SmallSmem {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
+__global__ void __launch_bounds__(kSmallWarps * 32, 2) k_build_small(RoundArgs a)
 {
     constexpr uint32_t KW = kSmallWords, NW = 32 * kSmallWords;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -1098,20 +1100,23 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
     const uint32_t h = rt.h, rb = rt.rb, n = jb.n;
     const bool matrix = a.kind == WT_MATRIX;
     const uint8_t *in = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
-    const uint32_t w0 = KW * lane;                    // this lane's words: w0 .. w0 + KW - 1
+    const uint32_t nj = (n + 1023u) / 1024u;          // rows of 32 words in use (1 .. KW)
+    const uint32_t nwu = 32u * nj;                    // words in use; word nwu takes overflow bits
 
     // ---- clear, load and transpose (plane k = code bit rb-1-k), class counts
-    for (uint32_t i = lane; i < 2 * kChunk * (NW + 1); i += 32) (&sm.plane[0][0][0])[i] = 0;
+    for (uint32_t k = 0; k < 2 * kChunk; ++k)
+        for (uint32_t i = lane; i <= nwu; i += 32) (&sm.plane[0][0][0])[k * (NW + 1) + i] = 0;
     for (uint32_t i = lane; i < kCols; i += 32) sm.hist[i] = 0;
     __syncwarp();
-    for (uint32_t j = 0; j < KW; ++j) {
+    for (uint32_t j = 0; j < nj; ++j) {
+        const uint32_t wj = 32u * j + lane;           // this lane's word of row j
         uint32_t x[8];
-        load32(in, rt.in_w, 32u * (w0 + j), n, 0u, x);
+        load32(in, rt.in_w, 32u * wj, n, 0u, x);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const uint32_t e = 32u * (w0 + j) + 4u * k + b;
+                const uint32_t e = 32u * wj + 4u * k + b;
                 if (e < n) atomicAdd(&sm.hist[(x[k] >> (8 * b)) & ((1u << h) - 1u)], 1u);
             }
         }
@@ -1123,7 +1128,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
             const bool hi = jb8 >= 4u;
             const uint32_t t01 = __byte_perm(hi ? x[1] : x[0], hi ? x[3] : x[2], sel);
             const uint32_t t23 = __byte_perm(hi ? x[5] : x[4], hi ? x[7] : x[6], sel);
-            sm.plane[0][k][w0 + j] = __byte_perm(t01, t23, 0x5410);
+            sm.plane[0][k][wj] = __byte_perm(t01, t23, 0x5410);
         }
     }
     __syncwarp();
@@ -1135,7 +1140,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
     if (matrix) {                                     // Z[c + l]: zeros of level l, any order
         for (uint32_t l = 0; l < h; ++l) {
             uint32_t z = 0;
-            for (uint32_t j = 0; j < KW; ++j) z += __popc(~sm.plane[0][l][w0 + j]);
+            for (uint32_t j = 0; j < nj; ++j) z += __popc(~sm.plane[0][l][32u * j + lane]);
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1) z += __shfl_xor_sync(kFull, z, d);
             if (lane == 0) t.zeros[rt.c + l] = z;
@@ -1171,22 +1176,25 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
                 return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
             },
             [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[q] = v; });
-        uint32_t mw[KW], zw[KW], zsum = 0;
-        for (uint32_t j = 0; j < KW; ++j) {
-            mw[j] = cur[l][w0 + j];
-            sm.lvl[w0 + j] = mw[j];
-            zw[j] = __popc(~mw[j]);
-            zsum += zw[j];
-        }
-        if (lane < 4) sm.lvl[NW + lane] = 0;
-        uint32_t inc = zsum;
+        // zeros before each of this lane's words (row by row: a warp scan plus
+        // the zeros of the rows before), and the total zt
+        uint32_t mw[KW], zw[KW], zb[KW], zt = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, inc, d);
-            if (lane >= (uint32_t)d) inc += y;
+        for (uint32_t j = 0; j < KW; ++j) {
+            if (j >= nj) break;
+            mw[j] = cur[l][32u * j + lane];
+            sm.lvl[32u * j + lane] = mw[j];
+            zw[j] = __popc(~mw[j]);
+            uint32_t inc = zw[j];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                if (lane >= (uint32_t)d) inc += y;
+            }
+            zb[j] = zt + inc - zw[j];
+            zt += __shfl_sync(kFull, inc, 31);
         }
-        const uint32_t zt = __shfl_sync(kFull, inc, 31);
-        uint32_t zo = inc - zsum;                     // zeros before word w0
+        if (lane < 4) sm.lvl[nwu + lane] = 0;
         __syncwarp();
         // ---- copy every class's bits to its interval start in level c + l
         uint64_t *lv = bv + (uint64_t)(rt.c + l) * t.W;
@@ -1214,24 +1222,26 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_build_small(RoundArgs a)
         }
         // ---- stable split of every later plane by plane l, word by word
         if (l + 1 < h) {
+#pragma unroll
             for (uint32_t j = 0; j < KW; ++j) {
-                const uint32_t m0 = mw[j], z0 = zw[j];
+                if (j >= nj) break;
+                const uint32_t wj = 32u * j + lane;
+                const uint32_t m0 = mw[j], z0 = zw[j], zo = zb[j];
                 uint32_t mz[5], mo[5];
                 compress_moves(~m0, mz);
                 compress_moves(m0, mo);
                 const uint32_t kz = z0 == 32u ? ~0u : (1u << z0) - 1u;
                 const uint32_t ko = z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u;
-                const uint32_t d1 = zt + 32u * (w0 + j) - zo;
+                const uint32_t d1 = zt + 32u * wj - zo;
                 for (uint32_t k = l + 1; k < h; ++k) {
-                    const uint32_t x = cur[k][w0 + j];
+                    const uint32_t x = cur[k][wj];
                     place_bits(nxt[k], zo, compress_apply(x, kz, mz), z0);
                     place_bits(nxt[k], d1, compress_apply(x, ko, mo), 32u - z0);
-                    cur[k][w0 + j] = 0;
+                    cur[k][wj] = 0;
                 }
-                zo += z0;
             }
             if (lane == 0)
-                for (uint32_t k = l + 1; k < h; ++k) cur[k][NW] = 0;
+                for (uint32_t k = l + 1; k < h; ++k) cur[k][nwu] = 0;
         }
         __syncwarp();
     }
