@@ -427,7 +427,9 @@ def run_ours(args):
     if rank != 0:
         return 0
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "bytes" and args.n_log2 is None
+        else f"input symbols/s, WT+WM construction ({desc})",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8" if w == 1 else f"u{8 * w}", "data": "synthetic",
         "config": {"workload": desc, "n": n, "sigma": sigma, "levels": L, "builds_per_step": 2,

@@ -83,6 +83,8 @@ __device__ __forceinline__ RoundText round_text(const TextInfo &t, uint32_t r)
 // Jobs of the last round of their text with at most kSmallJob symbols are built
 // by one warp each (k_build_small) and get no groups.
 constexpr uint32_t kSmallWords = 4;                  // words per lane of the warp build
+constexpr int kSmallWarps = 8;                        // warps per block of the 4-row instantiation
+constexpr int kTinyWarps = 16;                        // warps per block of the 1-row instantiation
 static_assert(kSmallJob == 32 * 32 * kSmallWords, "a small job is one warp's 32 x 32 x kSmallWords bits");
 
 __device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uint64_t n)
@@ -160,15 +162,18 @@ __device__ __forceinline__ void for_range(const void *base, uint32_t w, uint64_t
 
 // Exclusive scan of n <= 256 values by one warp: out[map(i)] = sum of
 // val(map(j)) for j < i.  Each lane takes 8 consecutive positions.
-template <typename V, typename M, typename O>
-__device__ __forceinline__ uint32_t warp_scan_256(uint32_t n, V val, M map, O out)
+template <bool FLEX, class V, class M, class O>
+__device__ __forceinline__ uint32_t warp_scan_t(uint32_t n, V val, M map, O out)
 {
-    const uint32_t lane = threadIdx.x & 31u;
+    // element i = lane * per + k: as many elements per lane as n needs (FLEX), or
+    // always 8 (fewer registers, for the kernel instantiations that are short of them)
+    const uint32_t lane = threadIdx.x & 31u, per = FLEX ? (n + 31u) >> 5 : 8u;
     uint32_t loc[8];
     uint32_t sum = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        uint32_t i = lane * 8 + k;
+    for (uint32_t k = 0; k < 8; ++k) {
+        if (k >= per) break;
+        const uint32_t i = lane * per + k;
         loc[k] = i < n ? val(map(i)) : 0u;
         sum += loc[k];
     }
@@ -180,12 +185,19 @@ __device__ __forceinline__ uint32_t warp_scan_256(uint32_t n, V val, M map, O ou
     }
     uint32_t run = inc - sum;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        uint32_t i = lane * 8 + k;
+    for (uint32_t k = 0; k < 8; ++k) {
+        if (k >= per) break;
+        const uint32_t i = lane * per + k;
         if (i < n) out(map(i), run);
         run += loc[k];
     }
     return __shfl_sync(kFull, inc, 31);
+}
+
+template <class V, class M, class O>
+__device__ __forceinline__ uint32_t warp_scan_256(uint32_t n, V val, M map, O out)
+{
+    return warp_scan_t<true>(n, val, map, out);
 }
 
 }  // namespace
@@ -714,7 +726,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     }
     __syncthreads();
     if (warp == 0) {
-        uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.cnt[i]; }, [](uint32_t i) { return i; },
+        uint32_t tot = warp_scan_t<!CUT>(256, [&](uint32_t i) { return sm.cnt[i]; }, [](uint32_t i) { return i; },
                                      [&](uint32_t i, uint32_t v) { sm.jP[i] = v; });
         if (lane == 0) sm.jP[256] = tot;
     }
@@ -729,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         const uint32_t l = j % (h + 1), base = 1u << l;   // j > h: the WM's starts (kBoth)
         const bool rv = matrix || j > h;
         uint32_t *dst = j > h ? sm.jspos2 : sm.jspos;
-        warp_scan_256(base, [&](uint32_t q) { return sm.jcnt[base + q]; },
+        warp_scan_t<!CUT>(base, [&](uint32_t q) { return sm.jcnt[base + q]; },
                       [&](uint32_t i) { return rv ? rev_bits(i, l) : i; },
                       [&](uint32_t q, uint32_t v) { dst[base + q] = v; });
     }
@@ -757,11 +769,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             sm.thc[q] = a.thist[((size_t)tile_first + tix) * kCols + q];
         __syncthreads();
         if (warp == 0) {
-            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.thc[i]; }, [](uint32_t i) { return i; },
+            uint32_t tot = warp_scan_t<!CUT>(256, [&](uint32_t i) { return sm.thc[i]; }, [](uint32_t i) { return i; },
                                          [&](uint32_t i, uint32_t v) { sm.tP[i] = v; });
             if (lane == 0) sm.tP[256] = tot;
         } else if (warp == 1) {
-            uint32_t tot = warp_scan_256(256, [&](uint32_t i) { return sm.offq[i]; }, [](uint32_t i) { return i; },
+            uint32_t tot = warp_scan_t<!CUT>(256, [&](uint32_t i) { return sm.offq[i]; }, [](uint32_t i) { return i; },
                                          [&](uint32_t i, uint32_t v) { sm.oP[i] = v; });
             if (lane == 0) sm.oP[256] = tot;
         }
@@ -783,13 +795,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         // prefixes, Obs. 2) and destination words of every class
         if (CUT && warp == h && (rt.cut != nullptr || t.perm != nullptr)) {   // class starts after the last split
             const uint32_t base = 1u << h;
-            warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
+            warp_scan_t<!CUT>(base, [&](uint32_t q) { return sm.cnt[base + q]; },
                           [&](uint32_t i) { return rev_bits(i, h); },
                           [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
         }
         if (warp < h) {                             // class starts in tile order (shared by kBoth)
             const uint32_t l = warp, base = 1u << l;
-            warp_scan_256(base, [&](uint32_t q) { return sm.cnt[base + q]; },
+            warp_scan_t<!CUT>(base, [&](uint32_t q) { return sm.cnt[base + q]; },
                           [&](uint32_t i) { return rev_bits(i, l); },
                           [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
         }
@@ -798,7 +810,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint32_t l = second ? warp - h : warp, base = 1u << l;
             const uint32_t *glo = second ? sm.glo2 : sm.glo;
             uint32_t *wpre = second ? sm.wpre2 : sm.wpre;
-            const uint32_t wt = warp_scan_256(
+            const uint32_t wt = warp_scan_t<!CUT>(
                 base,
                 [&](uint32_t q) {
                     const uint32_t c = sm.cnt[base + q];
@@ -1070,32 +1082,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 
 namespace {
 
-constexpr int kSmallWarps = 8;
-
+// Two instantiations: KW = 1 (jobs of at most 1024 symbols, most of the wavelet
+// tree's subtrees: 6 KB per warp, 16 warps per block) and KW = kSmallWords (the
+// rest, 8 warps per block).
+template <int KW>
 struct SmallSmem {
-    uint32_t plane[2][kChunk][32 * kSmallWords + 1];   // current / next planes (+ overflow word)
-    uint32_t lvl[32 * kSmallWords + 4];                // the current level's plane
+    uint32_t plane[2][kChunk][32 * KW + 1];   // current / next planes (+ overflow word)
+    uint32_t lvl[32 * KW + 4];                // the current level's plane
+    uint32_t lvl2[32 * KW + 4];               // WT: the level's plane in id order
     uint32_t hist[kCols];              // class counts of the job (leaf level)
     uint32_t P[kCols + 1];             // prefix sums of hist
     uint32_t cnt[kCols / 2];           // class counts of the current level
     uint32_t loc[kCols / 2];           // class start in job order (reversed prefixes)
     uint32_t glo[kCols / 2];           // class start inside the text's level
-    uint32_t wpre[kCols / 2];          // destination words before each class
 };
 
 }  // namespace
 
-__global__ void __launch_bounds__(kSmallWarps * 32, 2) k_build_small(RoundArgs a)
+template <int KW, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
 {
-    constexpr uint32_t KW = kSmallWords, NW = 32 * kSmallWords;
+    constexpr uint32_t NW = 32 * KW;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    SmallSmem &sm = reinterpret_cast<SmallSmem *>(smem_raw)[warp];
-    const uint32_t slot = blockIdx.x * kSmallWarps + warp;
+    SmallSmem<KW> &sm = reinterpret_cast<SmallSmem<KW> *>(smem_raw)[warp];
+    const uint32_t slot = blockIdx.x * WARPS + warp;
     if (slot >= a.nslots) return;
     const Job jb = a.jobs[slot];
     const TextInfo &t = a.texts[jb.text];
     if (!small_job(t, a.round, jb.n)) return;
+    if ((KW == 1) != (jb.n <= 1024u)) return;        // the other instantiation takes it
     const RoundText rt = round_text(t, a.round);
     const uint32_t h = rt.h, rb = rt.rb, n = jb.n;
     const bool matrix = a.kind == WT_MATRIX;
@@ -1160,22 +1176,10 @@ __global__ void __launch_bounds__(kSmallWarps * 32, 2) k_build_small(RoundArgs a
         warp_scan_256(base, [&](uint32_t q) { return sm.cnt[q]; }, [&](uint32_t i) { return rev_bits(i, l); },
                       [&](uint32_t q, uint32_t v) { sm.loc[q] = v; });
         __syncwarp();
-        if (matrix) {
-            for (uint32_t q = lane; q < base; q += 32) sm.glo[q] = jb.off + sm.loc[q];
-        } else {
-            warp_scan_256(base, [&](uint32_t q) { return sm.cnt[q]; }, [](uint32_t i) { return i; },
-                          [&](uint32_t q, uint32_t v) { sm.glo[q] = jb.off + v; });
-        }
+        // interval starts: the job's order for the WM; id order for the WT, where the
+        // symbols before prefix q are those with leaf codes below q << s
+        for (uint32_t q = lane; q < base; q += 32) sm.glo[q] = jb.off + (matrix ? sm.loc[q] : sm.P[q << s]);
         __syncwarp();
-        const uint32_t wt = warp_scan_256(
-            base,
-            [&](uint32_t q) {
-                const uint32_t c = sm.cnt[q];
-                if (c == 0) return 0u;
-                const uint32_t gs = sm.glo[q];
-                return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
-            },
-            [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { sm.wpre[q] = v; });
         // zeros before each of this lane's words (row by row: a warp scan plus
         // the zeros of the rows before), and the total zt
         uint32_t mw[KW], zw[KW], zb[KW], zt = 0;
@@ -1196,28 +1200,42 @@ __global__ void __launch_bounds__(kSmallWarps * 32, 2) k_build_small(RoundArgs a
         }
         if (lane < 4) sm.lvl[nwu + lane] = 0;
         __syncwarp();
-        // ---- copy every class's bits to its interval start in level c + l
-        uint64_t *lv = bv + (uint64_t)(rt.c + l) * t.W;
-        for (uint32_t k = lane; k < wt; k += 32) {
-            uint32_t lo = 0, hi = base;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (sm.wpre[mid] <= k) lo = mid; else hi = mid;
+        // ---- the job's bits of level c + l are the range [off, off + n) of the level:
+        //      for the WM in the job's order of classes (reversed prefixes, the
+        //      level's interval order); for the WT in id order, which differs from the
+        //      job's order from level 2 on: there the class runs are first moved to
+        //      their id-order places in lvl2
+        const uint32_t *src = sm.lvl;
+        if (!matrix && l >= 2) {
+            for (uint32_t i = lane; i < nwu + 4; i += 32) sm.lvl2[i] = 0;
+            __syncwarp();
+            for (uint32_t q = lane; q < base; q += 32) {
+                const uint32_t c = sm.cnt[q], from = sm.loc[q], to = sm.glo[q] - jb.off;
+                for (uint32_t i = 0; i < c; i += 64) {
+                    const uint32_t len = min(64u, c - i);
+                    place_bits(sm.lvl2, to + i, extract_bits(sm.lvl, from + i, len), len);
+                }
             }
-            const uint64_t gs = sm.glo[lo], ge = gs + sm.cnt[lo];
-            const uint64_t word = (gs >> 6) + (k - sm.wpre[lo]);
-            const uint64_t wb = word << 6;
-            const uint32_t blo = (uint32_t)((gs > wb ? gs : wb) - wb);
-            uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
-            const uint32_t src = sm.loc[lo] + (uint32_t)(wb + blo - gs);
-            const uint64_t val = extract_bits(sm.lvl, src, bhi - blo) << blo;
-            if (ge == t.n) bhi = 64;
-            if (blo == 0 && bhi == 64) {
-                lv[word] = val;
-            } else {
-                const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
-                atomicAnd(reinterpret_cast<unsigned long long *>(lv + word), ~msk);
-                atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
+            __syncwarp();
+            src = sm.lvl2;
+        }
+        {
+            uint64_t *lv = bv + (uint64_t)(rt.c + l) * t.W;
+            const uint64_t off = jb.off, end = off + n;
+            for (uint64_t d = (off >> 6) + lane; d <= (end - 1) >> 6; d += 32) {
+                const uint64_t wb = d << 6;
+                const uint64_t lo = wb > off ? wb : off, hi = end < wb + 64 ? end : wb + 64;
+                const uint32_t blo = (uint32_t)(lo - wb);
+                uint32_t bhi = (uint32_t)(hi - wb);
+                const uint64_t val = extract_bits(src, (uint32_t)(lo - off), bhi - blo) << blo;
+                if (end == t.n) bhi = 64;                  // bits past n belong to the last job
+                if (blo == 0 && bhi == 64) {
+                    lv[d] = val;
+                } else {
+                    const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
+                    atomicAnd(reinterpret_cast<unsigned long long *>(lv + d), ~msk);
+                    atomicOr(reinterpret_cast<unsigned long long *>(lv + d), val);
+                }
             }
         }
         // ---- stable split of every later plane by plane l, word by word
@@ -1252,8 +1270,11 @@ __global__ void __launch_bounds__(kSmallWarps * 32, 2) k_build_small(RoundArgs a
 cudaError_t configure_kernels()
 {
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_build_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(SmallSmem) * kSmallWarps));
+    e = cudaFuncSetAttribute(k_build_small<1, kTinyWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(SmallSmem<1>) * kTinyWarps));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_build_small<kSmallWords, kSmallWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(SmallSmem<kSmallWords>) * kSmallWarps));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
     if (e != cudaSuccess) return e;
@@ -1380,9 +1401,13 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     else
         k_build_bs<false, false><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
     if (a.any_plain && a.kind != kBoth)           // kBoth has no small jobs
-        k_build_small<<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
-                        sizeof(SmallSmem) * kSmallWarps, s>>>(a);
-    if (prof) profile_mark(0, false, s, (a.any_plain && a.kind != kBoth) ? 2 : 1);
+    {
+        k_build_small<1, kTinyWarps><<<(a.nslots + kTinyWarps - 1) / kTinyWarps, kTinyWarps * 32,
+                                      sizeof(SmallSmem<1>) * kTinyWarps, s>>>(a);
+        k_build_small<kSmallWords, kSmallWarps><<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
+                                                  sizeof(SmallSmem<kSmallWords>) * kSmallWarps, s>>>(a);
+    }
+    if (prof) profile_mark(0, false, s, (a.any_plain && a.kind != kBoth) ? 3 : 1);
     return cudaGetLastError();
 }
 
