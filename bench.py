@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (profiles/k_build_bs_bytes_n2e28_full.md)
-    "38a08768ec7561a6039c45022c786a71012f0ae62d811a067ce90ad215cd7400": {"dram_bytes": 345465344 + 222891520,
+    "d5676fbb876841a550a96560b70004f56341405b27363c5a14108aee8204f3e6": {"dram_bytes": 344817664 + 222893568,
                                                                          "n": 1 << 28},
 }
 
