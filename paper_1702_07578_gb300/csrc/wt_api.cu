@@ -28,7 +28,7 @@ struct Plan {
     uint32_t width[kMaxRounds] = {};
     uint32_t gelems[kMaxRounds] = {};     // symbols per build block in each round
     size_t off_ctl = 0, off_texts = 0, off_jobs[2] = {}, off_jobhist[2] = {};
-    size_t off_ghist = 0, off_gexcl = 0, off_thist = 0, off_btail = 0, off_bflag = 0, off_bcarry = 0;
+    size_t off_ghist = 0, off_gexcl = 0, off_thist = 0, off_btail = 0, off_bflag = 0, off_bcarry = 0, off_cscan = 0;
     std::vector<size_t> off_buf[2];
     std::vector<size_t> off_pbuf[2];      // text positions carried through cut rounds (perm)
     std::vector<TextInfo> texts;
@@ -154,6 +154,7 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
     p.off_btail = take(sizeof(uint32_t) * kCols * (size_t)max_blocks);
     p.off_bcarry = take(sizeof(uint32_t) * kCols * (size_t)max_blocks);
     p.off_bflag = take(sizeof(uint32_t) * (size_t)max_blocks);
+    p.off_cscan = take(sizeof(uint32_t) * 2 * ((size_t)max_slots / 4096 + 1));
     p.off_buf[0].assign(count, 0);
     p.off_buf[1].assign(count, 0);
     p.off_pbuf[0].assign(count, 0);
@@ -236,6 +237,7 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
         a.btail = reinterpret_cast<uint32_t *>(ws + p.off_btail);
         a.bflag = reinterpret_cast<uint32_t *>(ws + p.off_bflag);
         a.bcarry = reinterpret_cast<uint32_t *>(ws + p.off_bcarry);
+        a.cscan = reinterpret_cast<uint32_t *>(ws + p.off_cscan);
         a.ntexts = p.count;
         a.nslots = p.nslots[r];
         a.pnslots = r ? p.nslots[r - 1] : 0;
@@ -249,6 +251,11 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
             if (ti.nslots[r] == 0) continue;
             if (ti.L - kChunk * r > (uint32_t)kChunk) a.any_cut = 1; else a.any_plain = 1;
             if (ti.perm != nullptr) a.any_order = 1;
+            // small jobs (one warp each): the last round of a text that does not want its
+            // order, where the WT's subtrees (r >= 1) may be small, or the whole text is
+            if (ti.L - kChunk * r <= (uint32_t)kChunk && ti.perm == nullptr &&
+                ((kind == WT_TREE && r > 0) || (ti.n > 0 && ti.n <= kSmallJob)))
+                a.any_small = 1;
         }
         if (launch_round(a, p.width[r], s) != cudaSuccess) return WT_ERR_CUDA;
     }

@@ -96,6 +96,8 @@ struct RoundArgs {
     uint32_t any_cut;        // some job of the round writes a re-sorted text
     uint32_t any_plain;      // some job of the round has no cut (its text's last round)
     uint32_t any_order;      // some text of the round wants its stable order (perm)
+    uint32_t any_small;      // some job of the round may be small (one warp each)
+    uint32_t *cscan;         // [2 * chunks]: group and tile totals per 4096 slots (many-slot rounds)
 };
 
 // sorted[j] = text[perm[j]] for j < n (symbols of width w).

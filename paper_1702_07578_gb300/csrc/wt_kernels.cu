@@ -262,38 +262,46 @@ __global__ void __launch_bounds__(256) k_child_jobs(RoundArgs a)
 }
 
 // Exclusive scans over all slots of the group counts -> g0 (total groups) and
-// of the tile counts -> tile0, in chunks of 4096 slots (4 per thread).
-__global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
+// of the tile counts -> tile0, in chunks of 4096 slots (4 per thread).  One
+// block walks the chunks when there are few; with many (the wavelet tree's
+// rounds >= 1 of many texts) the chunks' totals are taken by one block each,
+// scanned, and every chunk is then written by its own block.
+constexpr uint32_t kScanChunk = 4096;
+constexpr uint32_t kScanOneBlock = 4 * kScanChunk;   // up to this many slots: one block
+
+// Scans chunk c0 .. c0 + 4095 with the carries in; writes g0 / tile0 when `write`.
+// Returns the chunk's totals through tg / tt (all threads).
+__device__ __forceinline__ void scan_chunk(const RoundArgs &a, uint32_t c0, uint32_t carry_g, uint32_t carry_t,
+                                           bool write, uint32_t *wg, uint32_t *wt, uint32_t &tg, uint32_t &tt)
 {
-    __shared__ uint32_t wg[32], wt[32];
     const uint32_t n = a.nslots, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    uint32_t carry_g = 0, carry_t = 0;
-    for (uint32_t c0 = 0; c0 < n; c0 += 4096) {
-        uint32_t ng[4], nt[4], sg = 0, st = 0;
+    uint32_t ng[4], nt[4], sg = 0, st = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t i = c0 + 4u * tid + j;
-            ng[j] = i < n ? a.jobs[i].ng : 0u;
-            nt[j] = i < n ? (a.jobs[i].n + kTileSyms - 1) / kTileSyms : 0u;
-            sg += ng[j];
-            st += nt[j];
-        }
-        uint32_t ig = sg, it = st;
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t i = c0 + 4u * tid + j;
+        ng[j] = i < n ? a.jobs[i].ng : 0u;
+        nt[j] = i < n ? (a.jobs[i].n + kTileSyms - 1) / kTileSyms : 0u;
+        sg += ng[j];
+        st += nt[j];
+    }
+    uint32_t ig = sg, it = st;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t yg = __shfl_up_sync(kFull, ig, d), yt = __shfl_up_sync(kFull, it, d);
-            if (lane >= (uint32_t)d) { ig += yg; it += yt; }
-        }
-        if (lane == 31) { wg[warp] = ig; wt[warp] = it; }
-        __syncthreads();
-        const uint32_t xg = wg[lane], xt = wt[lane];
-        uint32_t pg = xg, pt = xt;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t yg = __shfl_up_sync(kFull, ig, d), yt = __shfl_up_sync(kFull, it, d);
+        if (lane >= (uint32_t)d) { ig += yg; it += yt; }
+    }
+    if (lane == 31) { wg[warp] = ig; wt[warp] = it; }
+    __syncthreads();
+    const uint32_t xg = wg[lane], xt = wt[lane];
+    uint32_t pg = xg, pt = xt;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t yg = __shfl_up_sync(kFull, pg, d), yt = __shfl_up_sync(kFull, pt, d);
-            if (lane >= (uint32_t)d) { pg += yg; pt += yt; }
-        }
-        const uint32_t tg = __shfl_sync(kFull, pg, 31), tt = __shfl_sync(kFull, pt, 31);
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t yg = __shfl_up_sync(kFull, pg, d), yt = __shfl_up_sync(kFull, pt, d);
+        if (lane >= (uint32_t)d) { pg += yg; pt += yt; }
+    }
+    tg = __shfl_sync(kFull, pg, 31);
+    tt = __shfl_sync(kFull, pt, 31);
+    if (write) {
         uint32_t rg = carry_g + __shfl_sync(kFull, pg - xg, warp) + ig - sg;
         uint32_t rt_ = carry_t + __shfl_sync(kFull, pt - xt, warp) + it - st;
 #pragma unroll
@@ -306,11 +314,52 @@ __global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
             rg += ng[j];
             rt_ += nt[j];
         }
-        carry_g += tg;
-        carry_t += tt;
-        __syncthreads();
     }
-    if (tid == 0) a.ctl->total_groups[a.round] = carry_g;
+    __syncthreads();
+}
+
+// one block: every chunk in turn (few slots); or, with many slots, the scan of the
+// chunks' totals in a.cscan (exclusive, in place)
+__global__ void __launch_bounds__(1024) k_scan_groups(RoundArgs a)
+{
+    __shared__ uint32_t wg[32], wt[32];
+    const uint32_t n = a.nslots;
+    uint32_t carry_g = 0, carry_t = 0;
+    if (n <= kScanOneBlock) {
+        for (uint32_t c0 = 0; c0 < n; c0 += kScanChunk) {
+            uint32_t tg, tt;
+            scan_chunk(a, c0, carry_g, carry_t, true, wg, wt, tg, tt);
+            carry_g += tg;
+            carry_t += tt;
+        }
+    } else if (threadIdx.x == 0) {
+        const uint32_t chunks = (n + kScanChunk - 1) / kScanChunk;
+        for (uint32_t c = 0; c < chunks; ++c) {
+            const uint32_t g = a.cscan[2 * c], t = a.cscan[2 * c + 1];
+            a.cscan[2 * c] = carry_g;
+            a.cscan[2 * c + 1] = carry_t;
+            carry_g += g;
+            carry_t += t;
+        }
+    }
+    if (threadIdx.x == 0) a.ctl->total_groups[a.round] = carry_g;
+}
+
+// many slots: chunk blockIdx.x's totals (pass 0) or its slots written (pass 1)
+__global__ void __launch_bounds__(1024) k_scan_chunks(RoundArgs a, uint32_t pass)
+{
+    __shared__ uint32_t wg[32], wt[32];
+    const uint32_t c = blockIdx.x;
+    uint32_t tg, tt;
+    if (pass == 0) {
+        scan_chunk(a, c * kScanChunk, 0, 0, false, wg, wt, tg, tt);
+        if (threadIdx.x == 0) {
+            a.cscan[2 * c] = tg;
+            a.cscan[2 * c + 1] = tt;
+        }
+    } else {
+        scan_chunk(a, c * kScanChunk, a.cscan[2 * c], a.cscan[2 * c + 1], true, wg, wt, tg, tt);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1384,7 +1433,14 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     if (prof) profile_mark(3, true, s);
     if (root) k_root_jobs<<<(a.ntexts + 255) / 256, 256, 0, s>>>(a);
     else k_child_jobs<<<a.pnslots, 256, 0, s>>>(a);
-    k_scan_groups<<<1, 1024, 0, s>>>(a);
+    if (a.nslots <= kScanOneBlock) {
+        k_scan_groups<<<1, 1024, 0, s>>>(a);
+    } else {
+        const uint32_t chunks = (a.nslots + kScanChunk - 1) / kScanChunk;
+        k_scan_chunks<<<chunks, 1024, 0, s>>>(a, 0u);
+        k_scan_groups<<<1, 1024, 0, s>>>(a);
+        k_scan_chunks<<<chunks, 1024, 0, s>>>(a, 1u);
+    }
     if (prof) profile_mark(3, false, s);
     if (a.groups_ub == 0) return cudaGetLastError();
     if (prof) profile_mark(1, true, s);
@@ -1400,14 +1456,14 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
         k_build_bs<false, true><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
     else
         k_build_bs<false, false><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
-    if (a.any_plain && a.kind != kBoth)           // kBoth has no small jobs
+    if (a.any_small && a.kind != kBoth)           // kBoth has no small jobs
     {
         k_build_small<1, kTinyWarps><<<(a.nslots + kTinyWarps - 1) / kTinyWarps, kTinyWarps * 32,
                                       sizeof(SmallSmem<1>) * kTinyWarps, s>>>(a);
         k_build_small<kSmallWords, kSmallWarps><<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
                                                   sizeof(SmallSmem<kSmallWords>) * kSmallWarps, s>>>(a);
     }
-    if (prof) profile_mark(0, false, s, (a.any_plain && a.kind != kBoth) ? 3 : 1);
+    if (prof) profile_mark(0, false, s, (a.any_small && a.kind != kBoth) ? 3 : 1);
     return cudaGetLastError();
 }
 
