@@ -98,16 +98,16 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
         ti.sigma = x.sigma;
         ti.L = L;
         ti.in_w = w;
-        const uint32_t rounds = (L + kChunk - 1) / kChunk;
+        const uint32_t rounds = round_count(L);
         if (rounds > p.rounds) p.rounds = rounds;
         for (uint32_t r = 0; r < kMaxRounds; ++r) {
-            uint32_t ns = 0;
-            if (x.n > 0 && L > kChunk * r) ns = (kind == WT_TREE) ? (1u << (8 * r)) : 1u;
+            uint32_t ns = 0;                          // WT: one slot per prefix of the levels done
+            if (x.n > 0 && r < rounds) ns = (kind == WT_TREE) ? (1u << round_first_level(L, r)) : 1u;
             ti.nslots[r] = ns;
             ti.slot_base[r] = (uint32_t)slot_acc[r];
             slot_acc[r] += ns;
             if (ns) {
-                uint32_t wr = width_for_bits(L - kChunk * r);
+                uint32_t wr = width_for_bits(L - round_first_level(L, r));
                 if (wr > width[r]) width[r] = wr;
             }
         }
@@ -162,10 +162,13 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
     for (uint32_t i = 0; i < count; ++i) {
         const TextInfo &ti = p.texts[i];
         if (ti.n == 0) continue;
-        if (ti.L > kChunk) p.off_buf[0][i] = take(ti.n * width_for_bits(ti.L - kChunk));
-        if (ti.L > 2 * kChunk) p.off_buf[1][i] = take(ti.n * width_for_bits(ti.L - 2 * kChunk));
-        if (t[i].order && ti.L > kChunk) p.off_pbuf[0][i] = take(ti.n * sizeof(uint32_t));
-        if (t[i].order && ti.L > 2 * kChunk) p.off_pbuf[1][i] = take(ti.n * sizeof(uint32_t));
+        // round r's re-sorted output (r = 0, 1; later rounds reuse them) holds the
+        // code bits still to split after it
+        const uint32_t R = round_count(ti.L);
+        if (R > 1) p.off_buf[0][i] = take(ti.n * width_for_bits(ti.L - round_first_level(ti.L, 1)));
+        if (R > 2) p.off_buf[1][i] = take(ti.n * width_for_bits(ti.L - round_first_level(ti.L, 2)));
+        if (t[i].order && R > 1) p.off_pbuf[0][i] = take(ti.n * sizeof(uint32_t));
+        if (t[i].order && R > 2) p.off_pbuf[1][i] = take(ti.n * sizeof(uint32_t));
     }
     p.bytes = off;
     return WT_OK;
@@ -195,10 +198,11 @@ wt_status prepare(Plan &p, void *d_ws, size_t ws_bytes)
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
     for (uint32_t i = 0; i < p.count; ++i) {
         TextInfo &ti = p.texts[i];
-        ti.buf[0] = ti.L > kChunk ? ws + p.off_buf[0][i] : nullptr;
-        ti.buf[1] = ti.L > 2 * kChunk ? ws + p.off_buf[1][i] : nullptr;
-        ti.pbuf[0] = ti.perm && ti.L > kChunk ? reinterpret_cast<uint32_t *>(ws + p.off_pbuf[0][i]) : nullptr;
-        ti.pbuf[1] = ti.perm && ti.L > 2 * kChunk ? reinterpret_cast<uint32_t *>(ws + p.off_pbuf[1][i]) : nullptr;
+        const uint32_t R = round_count(ti.L);
+        ti.buf[0] = R > 1 ? ws + p.off_buf[0][i] : nullptr;
+        ti.buf[1] = R > 2 ? ws + p.off_buf[1][i] : nullptr;
+        ti.pbuf[0] = ti.perm && R > 1 ? reinterpret_cast<uint32_t *>(ws + p.off_pbuf[0][i]) : nullptr;
+        ti.pbuf[1] = ti.perm && R > 2 ? reinterpret_cast<uint32_t *>(ws + p.off_pbuf[1][i]) : nullptr;
     }
     return WT_OK;
 }
@@ -249,11 +253,12 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
         for (uint32_t i = 0; i < p.count; ++i) {
             const TextInfo &ti = p.texts[i];
             if (ti.nslots[r] == 0) continue;
-            if (ti.L - kChunk * r > (uint32_t)kChunk) a.any_cut = 1; else a.any_plain = 1;
+            const bool last = r + 1 == round_count(ti.L);
+            if (!last) a.any_cut = 1; else a.any_plain = 1;
             if (ti.perm != nullptr) a.any_order = 1;
             // small jobs (one warp each): the last round of a text that does not want its
             // order, where the WT's subtrees (r >= 1) may be small, or the whole text is
-            if (ti.L - kChunk * r <= (uint32_t)kChunk && ti.perm == nullptr &&
+            if (last && ti.perm == nullptr &&
                 ((kind == WT_TREE && r > 0) || (ti.n > 0 && ti.n <= kSmallJob)))
                 a.any_small = 1;
         }

@@ -1,13 +1,14 @@
 // Internal definitions shared by the CUDA translation units of wt_gb300.
 //
-// Construction is organised in rounds of at most 8 levels (levels 8r .. 8r+7).
-// Round r works on "jobs": contiguous runs of symbols of one text whose
-// remaining rb = L - 8r code bits are still to be split.  Round 0 has one job
-// per text.  For the wavelet matrix every round has one job per text (the text
-// stably re-sorted by the reversed 8r-bit prefix, Obs. 2).  For the wavelet
-// tree, round r >= 1 has one job per (8r)-bit prefix: the independent subtree
-// below that prefix (Sec. 2, node definition), stored contiguously because the
-// previous round wrote the text stably sorted by prefix (Obs. 1).
+// Construction is organised in rounds of at most 8 levels (the first round takes
+// L mod 8 levels, the others 8; see round_first_level).  Round r works on "jobs":
+// contiguous runs of symbols of one text whose remaining rb code bits are still
+// to be split.  Round 0 has one job per text.  For the wavelet matrix every round
+// has one job per text (the text stably re-sorted by the reversed prefix of the
+// levels done, Obs. 2).  For the wavelet tree, round r >= 1 has one job per
+// prefix of the levels done: the independent subtree below that prefix (Sec. 2,
+// node definition), stored contiguously because the previous round wrote the text
+// stably sorted by prefix (Obs. 1).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -36,6 +37,21 @@ constexpr uint32_t kSmallJob = 4096;  // jobs of the last round up to this size:
 
 // Default symbols per build block: two tiles.
 constexpr uint32_t kDefaultGroup = 2 * 32768;
+
+// Round geometry.  A text of L levels is built in ceil(L / 8) rounds; the first
+// takes the L mod 8 top levels (8 when L is a multiple of 8) and every later round
+// 8, so that the last round, where the wavelet tree has one job per subtree, has
+// the fewest and largest subtrees.
+__host__ __device__ inline uint32_t round_count(uint32_t L) { return (L + kChunk - 1) / kChunk; }
+__host__ __device__ inline uint32_t first_round_levels(uint32_t L) { return L ? (L - 1) % kChunk + 1 : 0; }
+__host__ __device__ inline uint32_t round_first_level(uint32_t L, uint32_t r)
+{
+    return r ? first_round_levels(L) + kChunk * (r - 1) : 0;
+}
+__host__ __device__ inline uint32_t round_levels(uint32_t L, uint32_t r)
+{
+    return r ? kChunk : first_round_levels(L);
+}
 
 // Smallest storage width (bytes) that holds b-bit codes.
 __host__ __device__ inline uint32_t width_for_bits(uint32_t b) { return b <= 8 ? 1u : (b <= 16 ? 2u : 4u); }

@@ -70,9 +70,9 @@ struct RoundText {
 __device__ __forceinline__ RoundText round_text(const TextInfo &t, uint32_t r)
 {
     RoundText x;
-    x.c = kChunk * r;
+    x.c = round_first_level(t.L, r);
     x.rb = t.L - x.c;
-    x.h = x.rb < (uint32_t)kChunk ? x.rb : (uint32_t)kChunk;
+    x.h = round_levels(t.L, r);
     x.in = r == 0 ? t.text : t.buf[(r - 1) & 1];
     x.in_w = r == 0 ? t.in_w : width_for_bits(x.rb);
     x.cut = x.rb > x.h ? t.buf[r & 1] : nullptr;
@@ -90,7 +90,7 @@ static_assert(kSmallJob == 32 * 32 * kSmallWords, "a small job is one warp's 32 
 __device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uint64_t n)
 {
     // texts that want the stable order take the block path, which ranks it
-    return n > 0 && n <= kSmallJob && t.L - kChunk * round <= (uint32_t)kChunk && t.perm == nullptr;
+    return n > 0 && n <= kSmallJob && t.L - round_first_level(t.L, round) <= (uint32_t)kChunk && t.perm == nullptr;
 }
 
 // Lanes whose 8-bit key equals this lane's, among the lanes with ok set: the AND
@@ -231,9 +231,10 @@ __global__ void k_root_jobs(RoundArgs a)
     a.jobs[x.slot_base[a.round]] = j;
 }
 
-// WT round r >= 1: parent job p splits into 256 children, one per class of the
-// parent's last level; child q starts at the parent's start plus the
-// zero-based prefix sum of the parent's class totals in id order (Sec. 3.1).
+// WT round r >= 1: parent job p splits into 2^h children (h: the levels of the
+// parent's round), one per class of the parent's last level; child q starts at
+// the parent's start plus the zero-based prefix sum of the parent's class totals
+// in id order (Sec. 3.1).
 __global__ void __launch_bounds__(256) k_child_jobs(RoundArgs a)
 {
     __shared__ uint32_t s[256];
@@ -250,7 +251,9 @@ __global__ void __launch_bounds__(256) k_child_jobs(RoundArgs a)
                       [&](uint32_t i, uint32_t v) { s[i] = v; });
     }
     __syncthreads();
-    uint32_t cb = x.slot_base[a.round] + (p - x.slot_base[a.round - 1]) * 256u;
+    const uint32_t hp = round_levels(x.L, a.round - 1);
+    if (q >= (1u << hp)) return;                      // the parent has 2^hp classes
+    const uint32_t cb = x.slot_base[a.round] + ((p - x.slot_base[a.round - 1]) << hp);
     Job j;
     j.n = cnt;
     j.off = pj.off + s[q];
