@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (profiles/k_build_bs_bytes_n2e28_full.md)
-    "d5676fbb876841a550a96560b70004f56341405b27363c5a14108aee8204f3e6": {"dram_bytes": 344817664 + 222893568,
+    "b38380557545bd8a36370d21ee28e7d21a26f8e5eaf5d6bdab05a6f2a602428d": {"dram_bytes": 344877568 + 222808320,
                                                                          "n": 1 << 28},
 }
 
