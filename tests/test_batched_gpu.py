@@ -133,3 +133,29 @@ def test_graph_plan_replay_and_update(kind, tmp_path, monkeypatch):
                 assert np.array_equal(to_u64(bv[i]), e), i
                 assert np.array_equal(zz[i][:e.shape[0]].cpu().numpy().astype(np.uint64), ez)
     plan.close()
+
+
+@pytest.mark.parametrize("kind", ["wt", "wm"])
+def test_batched_mixed_round_geometry(kind):
+    """One batch whose texts have 1, 2 and 3 rounds of different first-round lengths
+    (L = 2, 9, 12, 13, 17, 20, 24): round r mixes texts with different prefixes done,
+    different children per parent and texts that are already finished."""
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    rng = np.random.default_rng(2024)
+    sigmas = [3, 300, 4096, 5000, 70000, 1 << 20, 1 << 24, 300, 5000, 1 << 20]
+    lengths = [1000, 50000, 70001, 12345, 90000, 130000, 60000, 0, 1, 4097]
+    texts = [synth.zipf_text(n, s, 0.9, int(rng.integers(1, 1 << 30)), np.uint32) if n else np.zeros(0, np.uint32)
+             for n, s in zip(lengths, sigmas)]
+    k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+    bvs, zs = wtg.wt_build_batched(k, [torch_text(t) if t.size else torch.zeros(0, dtype=torch.int32, device="cuda")
+                                       for t in texts], sigmas)
+    torch.cuda.synchronize()
+    for i, (T, sigma) in enumerate(zip(texts, sigmas)):
+        if kind == "wt":
+            assert np.array_equal(to_u64(bvs[i]), oracle.wt(T, sigma)), f"text {i} sigma {sigma}"
+        else:
+            e, ez = oracle.wm(T, sigma)
+            assert np.array_equal(to_u64(bvs[i]), e), f"text {i} sigma {sigma}"
+            assert np.array_equal(zs[i][:e.shape[0]].cpu().numpy().astype(np.uint64), ez)
