@@ -111,3 +111,41 @@ def test_pinned_submit_matches_copy_submit():
     with pytest.raises(ValueError):
         srv.submit(wtg.WT_TREE, pageable, reqs[0][2])
     srv.close()
+
+
+def test_concurrent_submitters():
+    """Four host threads submit, wait, read and release at the same time (the C calls
+    run without the interpreter lock); every result equals the oracle."""
+    import threading
+
+    import paper_1702_07578_gb300 as wtg
+    reqs = _requests(32, 123, max_log=16)
+    srv = wtg.WtServer(hbm_budget_bytes=1 << 30, max_batch=6, streams=3)
+    errors = []
+
+    def worker(part):
+        try:
+            for k, T, sg in part:
+                kind = wtg.WT_TREE if k == "wt" else wtg.WT_MATRIX
+                t = srv.submit(kind, T, sg)
+                r = srv.wait(t, timeout_us=60_000_000)
+                assert r["status"] == 0
+                bv, z = srv.read(t)
+                srv.release(t)
+                if k == "wt":
+                    assert np.array_equal(bv, oracle.wt(T, sg))
+                else:
+                    e, ez = oracle.wm(T, sg)
+                    assert np.array_equal(bv, e) and np.array_equal(z, ez)
+        except Exception as exc:          # reported on the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=worker, args=(reqs[i::4],)) for i in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    st = srv.stats()
+    srv.close()
+    assert not errors, errors[0]
+    assert st["completed"] == len(reqs)
