@@ -444,6 +444,12 @@ def run_ours(args):
     }
     if fused is not None:
         line["fused"] = fused
+    # device memory of one build per input byte, the paper's measure (Table 3): the
+    # text, the L bit vectors (+ Z) and the workspace
+    out_b = L * W * 8
+    line["memory"] = {"text_bytes": n * w, "output_bytes": out_b, "workspace_bytes_wt": ws_t.numel(),
+                      "workspace_bytes_wm": ws_m.numel(),
+                      "bytes_per_input_byte": (n * w + out_b + max(ws_t.numel(), ws_m.numel())) / (n * w)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(T, sigma, args.oracle_sample_log2)
     print(json.dumps(line), flush=True)
