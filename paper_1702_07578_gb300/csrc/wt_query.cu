@@ -153,16 +153,37 @@ __device__ __forceinline__ uint32_t block_scan_1024(uint32_t v, uint32_t *ws, ui
     return before + inc - v;
 }
 
+// ones of 256-bit block b of level l: two 16-byte loads when the block is whole and
+// the level row is 16-byte aligned, else word by word
+__device__ __forceinline__ uint32_t block_ones_v(const QArgs &a, uint32_t l, uint64_t b, bool vec)
+{
+    if (vec && b * 4 + 4 <= a.W) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(a.bv + (uint64_t)l * a.W + b * 4);
+        const uint4 x = __ldg(q), y = __ldg(q + 1);
+        return __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w) + __popc(y.x) + __popc(y.y) +
+               __popc(y.z) + __popc(y.w);
+    }
+    return block_ones(a, l, b);
+}
+
+// Block b0 + 1024 j + t of a chunk belongs to thread t (j = 0..3): a warp reads 32
+// consecutive blocks (1 KB) per j.
+__device__ __forceinline__ bool rows_aligned(const QArgs &a)
+{
+    return (a.W % 2 == 0) && (reinterpret_cast<uintptr_t>(a.bv) % 16 == 0);
+}
+
 // grid (nchunks, L), 1024 threads: ones of each chunk of 4096 blocks
 __global__ void __launch_bounds__(1024) k_dir_chunks(QArgs a)
 {
     __shared__ uint32_t ws[32];
     const uint32_t l = blockIdx.y;
     const uint64_t b0 = (uint64_t)blockIdx.x * kDirChunk;
+    const bool vec = rows_aligned(a);
     uint32_t s = 0;
     for (uint32_t j = 0; j < 4; ++j) {
-        const uint64_t b = b0 + threadIdx.x * 4 + j;
-        if (b + 1 < a.NB) s += block_ones(a, l, b);
+        const uint64_t b = b0 + j * 1024 + threadIdx.x;
+        if (b + 1 < a.NB) s += block_ones_v(a, l, b, vec);
     }
     uint32_t total;
     block_scan_1024(s, ws, &total);
@@ -185,24 +206,22 @@ __global__ void __launch_bounds__(1024) k_dir_chunk_scan(QArgs a)
     }
 }
 
-// grid (nchunks, L), 1024 threads: exclusive prefix of every block
+// grid (nchunks, L), 1024 threads: exclusive prefix of every block (blocks in
+// order: row j of 1024, then thread t)
 __global__ void __launch_bounds__(1024) k_dir_apply(QArgs a)
 {
     __shared__ uint32_t ws[32];
     const uint32_t l = blockIdx.y;
     const uint64_t b0 = (uint64_t)blockIdx.x * kDirChunk;
-    uint32_t c[4], s = 0;
+    const bool vec = rows_aligned(a);
+    uint32_t run = a.csum[(uint64_t)l * a.nchunks + blockIdx.x];
     for (uint32_t j = 0; j < 4; ++j) {
-        const uint64_t b = b0 + threadIdx.x * 4 + j;
-        c[j] = b + 1 < a.NB ? block_ones(a, l, b) : 0u;
-        s += c[j];
-    }
-    uint32_t total;
-    uint32_t run = a.csum[(uint64_t)l * a.nchunks + blockIdx.x] + block_scan_1024(s, ws, &total);
-    for (uint32_t j = 0; j < 4; ++j) {
-        const uint64_t b = b0 + threadIdx.x * 4 + j;
-        if (b < a.NB) a.dirw[(uint64_t)l * a.NB + b] = run;
-        run += c[j];
+        const uint64_t b = b0 + j * 1024 + threadIdx.x;
+        const uint32_t c = b + 1 < a.NB ? block_ones_v(a, l, b, vec) : 0u;
+        uint32_t total;
+        const uint32_t ex = block_scan_1024(c, ws, &total);
+        if (b < a.NB) a.dirw[(uint64_t)l * a.NB + b] = run + ex;
+        run += total;
     }
 }
 
