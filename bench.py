@@ -854,11 +854,29 @@ def run_queries(args):
             e1.record()
             torch.cuda.synchronize()
             res[f"{name}_{op}_per_s"] = q * args.steps / (e0.elapsed_time(e1) / 1e3)
+        if kind == wtg.WT_TREE:
+            # Lemma 3: the WT -> WM position map (built from the WT's rank support),
+            # then random (level, position) pairs mapped
+            e0.record()
+            m = wtg.WtToWmMap(idx)
+            e1.record()
+            torch.cuda.synchronize()
+            res["wt2wm_build_ms"] = e0.elapsed_time(e1)
+            lv = torch.randint(0, wtg.wt_levels(sigma), (q,), device="cuda", generator=g, dtype=torch.int32)
+            m(lv, pos)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.steps):
+                m(lv, pos)
+            e1.record()
+            torch.cuda.synchronize()
+            res["wt2wm_per_s"] = q * args.steps / (e0.elapsed_time(e1) / 1e3)
+            del m
         del idx, bv, z
     if rank != 0:
         return 0
     line = {
-        "metric": "queries/s on a built WT and WM (access, rank, select), n = 2^30 uint8, sigma = 256",
+        "metric": "queries/s on a built WT and WM (access, rank, select; Lemma 3 map), n = 2^30 uint8, sigma = 256",
         "value": res["wm_access_per_s"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
