@@ -13,12 +13,14 @@ namespace wtg {
 namespace {
 
 constexpr uint32_t kDirChunk = 4096;       // directory entries per scan chunk
+constexpr uint32_t kSampleLog = 13;        // select samples: every 8192nd one / zero of a level
 constexpr uint64_t kNone = ~0ull;
 
 struct RsLayout {
     uint32_t L = 0;
     uint64_t W = 0, NB = 0, nchunks = 0;
-    size_t off_dir = 0, off_csum = 0, off_S = 0, off_R = 0, bytes = 0;
+    uint64_t NS = 0;                        // select samples per level and bit value
+    size_t off_dir = 0, off_csum = 0, off_S = 0, off_R = 0, off_smp = 0, bytes = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -49,6 +51,11 @@ wt_status layout(wt_kind kind, uint64_t n, uint64_t sigma, RsLayout &r)
     off = align256(off + sizeof(uint32_t) * tbl);
     r.off_R = off;
     off = align256(off + sizeof(uint32_t) * tbl);
+    // block of the (k * 8192)-th one and zero of every level (the zeros counted over
+    // whole blocks, the padding past n last)
+    r.NS = ((r.NB - 1) * 256 >> kSampleLog) + 2;
+    r.off_smp = off;
+    off = align256(off + sizeof(uint32_t) * 2 * r.L * r.NS);
     r.bytes = off > 0 ? off : 256;
     return WT_OK;
 }
@@ -60,7 +67,8 @@ struct QArgs {
     uint32_t *dirw;           // same, writable (build)
     uint32_t *csum;           // L * nchunks
     uint32_t *S, *R;          // WT node starts / ones before them, level l at (2^l - 1 + l)
-    uint64_t n, W, NB, nchunks;
+    uint32_t *smp;            // select samples [level][bit value][NS] (null: search the whole directory)
+    uint64_t n, W, NB, nchunks, NS;
     uint32_t L;
     uint32_t kind;
 };
@@ -105,6 +113,13 @@ __device__ __forceinline__ uint64_t select_bit(const QArgs &a, uint32_t l, uint6
     const uint64_t *bv = a.bv + (uint64_t)l * a.W;
     const uint32_t *dir = a.dir + (uint64_t)l * a.NB;
     uint64_t lo = 0, hi = a.NB - 1;                         // last block with count-before <= j
+    if (a.smp != nullptr) {                                 // the samples around j bound the search
+        const uint32_t *sm = a.smp + ((uint64_t)l * 2 + (one ? 1 : 0)) * a.NS;
+        const uint64_t k = j >> kSampleLog;
+        lo = sm[k];
+        const uint64_t total = one ? dir[a.NB - 1] : (a.NB - 1) * 256 - dir[a.NB - 1];
+        if (((k + 1) << kSampleLog) < total) hi = (uint64_t)sm[k + 1] + 1;
+    }
     while (hi - lo > 1) {
         const uint64_t mid = (lo + hi) >> 1;
         const uint64_t before = one ? dir[mid] : mid * 256 - dir[mid];
@@ -223,6 +238,22 @@ __global__ void __launch_bounds__(1024) k_dir_apply(QArgs a)
         if (b < a.NB) a.dirw[(uint64_t)l * a.NB + b] = run + ex;
         run += total;
     }
+}
+
+// grid (blocks, L): block b records itself as the sample of every (k * 8192)-th one
+// and zero it holds
+__global__ void k_select_samples(QArgs a)
+{
+    const uint32_t l = blockIdx.y;
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b + 1 >= a.NB) return;
+    const uint32_t *dir = a.dir + (uint64_t)l * a.NB;
+    const uint64_t o0 = dir[b], o1 = dir[b + 1];
+    const uint64_t z0 = b * 256 - o0, z1 = (b + 1) * 256 - o1;
+    uint32_t *s1 = a.smp + ((uint64_t)l * 2 + 1) * a.NS, *s0 = a.smp + (uint64_t)l * 2 * a.NS;
+    const uint64_t S = 1ull << kSampleLog;
+    for (uint64_t k = (o0 + S - 1) >> kSampleLog; (k << kSampleLog) < o1; ++k) s1[k] = (uint32_t)b;
+    for (uint64_t k = (z0 + S - 1) >> kSampleLog; (k << kSampleLog) < z1; ++k) s0[k] = (uint32_t)b;
 }
 
 // WT node tables, level l: node p covers [S[p], S[p+1]); R[p] = ones before S[p]
@@ -377,6 +408,8 @@ QArgs make_args(const RsLayout &r, wt_kind kind, const uint64_t *bv, const uint6
     a.csum = reinterpret_cast<uint32_t *>(base + r.off_csum);
     a.S = reinterpret_cast<uint32_t *>(base + r.off_S);
     a.R = reinterpret_cast<uint32_t *>(base + r.off_R);
+    a.smp = reinterpret_cast<uint32_t *>(base + r.off_smp);
+    a.NS = r.NS;
     a.n = n;
     a.W = r.W;
     a.NB = r.NB;
@@ -427,6 +460,7 @@ wt_status wt_rank_support_build(wt_kind kind, const uint64_t *d_bv, const uint64
     k_dir_chunks<<<grid, 1024, 0, s>>>(a);
     k_dir_chunk_scan<<<r.L, 1024, 0, s>>>(a);
     k_dir_apply<<<grid, 1024, 0, s>>>(a);
+    k_select_samples<<<dim3((uint32_t)((r.NB + 255) / 256), r.L), 256, 0, s>>>(a);
     if (kind == WT_TREE)
         for (uint32_t l = 0; l < r.L; ++l) {
             const uint64_t threads = (1ull << l) + 1;
