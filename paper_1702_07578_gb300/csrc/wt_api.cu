@@ -48,6 +48,10 @@ uint32_t levels_of(uint64_t sigma)
 // choice (a multiple of it) fits in a workspace of the reported size.
 constexpr uint32_t kMinSpb = 32768;
 
+// Rounds with fewer symbols than this many default groups (one wave of two build
+// blocks per SM on 152 SMs) get one-tile groups, so that more blocks share the work.
+constexpr uint32_t kSmallRoundGroups = 2 * 152;
+
 bool valid_spb(uint32_t spb) { return spb == 0 || (spb % kMinSpb == 0 && spb <= (1u << 24)); }
 
 // Checks the texts and lays out the workspace.  With check_ptrs == false only
@@ -116,6 +120,12 @@ wt_status make_plan(wt_kind kind, wt_symtype type, const HostText *t, uint32_t c
         if (slot_acc[r] >= (1ull << 31)) return WT_ERR_INVALID_ARG;
         p.width[r] = width[r] ? width[r] : 1;
         p.gelems[r] = spb ? spb : kDefaultGroup;
+        if (!spb) {                   // less than one wave of default groups: one tile per group
+            uint64_t syms = 0;
+            for (uint32_t i = 0; i < count; ++i)
+                if (p.texts[i].nslots[r]) syms += p.texts[i].n;
+            if (syms < (uint64_t)kSmallRoundGroups * kDefaultGroup) p.gelems[r] = kMinSpb;
+        }
         const uint64_t ge = p.gelems[r];
         for (uint32_t i = 0; i < count; ++i) {
             const TextInfo &ti = p.texts[i];
