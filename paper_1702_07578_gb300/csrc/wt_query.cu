@@ -298,13 +298,23 @@ __device__ __forceinline__ uint32_t cbit(uint32_t c, uint32_t l, uint32_t L) { r
 __device__ uint64_t rank_sym(const QArgs &a, uint32_t c, uint64_t i)
 {
     if (a.kind == WT_TREE) {
+        // the node path is c's prefixes: each level's node entries are loaded one
+        // level ahead, so a level waits for its rank only
         uint64_t k = i, p = 0;
+        uint32_t s = a.S[tbl_off(0)], r = a.R[tbl_off(0)];
         for (uint32_t l = 0; l < a.L; ++l) {
-            const uint32_t s = a.S[tbl_off(l) + p];
-            const uint64_t ones = rank1(a, l, s + k) - a.R[tbl_off(l) + p];
             const uint32_t b = cbit(c, l, a.L);
+            const uint64_t pn = 2 * p + b;
+            uint32_t sn = 0, rn = 0;
+            if (l + 1 < a.L) {
+                sn = a.S[tbl_off(l + 1) + pn];
+                rn = a.R[tbl_off(l + 1) + pn];
+            }
+            const uint64_t ones = rank1(a, l, s + k) - r;
             k = b ? ones : k - ones;
-            p = 2 * p + b;
+            p = pn;
+            s = sn;
+            r = rn;
         }
         return k;
     }
@@ -330,16 +340,28 @@ __global__ void k_access(QArgs a, const uint64_t *pos, uint32_t count, uint32_t 
     if (i >= a.n) { out[k] = 0xffffffffu; return; }
     uint32_t sym = 0;
     if (a.kind == WT_TREE) {
+        // both children's starts and ones-before are loaded with the level's own
+        // reads, so a level costs one round trip to memory
         uint64_t p = 0;
+        uint32_t s = a.S[tbl_off(0)], r = a.R[tbl_off(0)];
         for (uint32_t l = 0; l < a.L; ++l) {
             const uint64_t *bv = a.bv + (uint64_t)l * a.W;
+            uint32_t s0 = 0, s1 = 0, r0 = 0, r1 = 0;
+            if (l + 1 < a.L) {
+                const size_t o = tbl_off(l + 1) + 2 * p;
+                s0 = a.S[o];
+                s1 = a.S[o + 1];
+                r0 = a.R[o];
+                r1 = a.R[o + 1];
+            }
             const uint32_t b = (uint32_t)(bv[i >> 6] >> (i & 63)) & 1u;
-            const uint32_t s = a.S[tbl_off(l) + p];
-            const uint64_t ones = rank1(a, l, i) - a.R[tbl_off(l) + p];
+            const uint64_t ones = rank1(a, l, i) - r;
             sym = (sym << 1) | b;
             if (l + 1 < a.L) {
+                i = (b ? s1 : s0) + (b ? ones : (i - s) - ones);
                 p = 2 * p + b;
-                i = a.S[tbl_off(l + 1) + p] + (b ? ones : (i - s) - ones);
+                s = b ? s1 : s0;
+                r = b ? r1 : r0;
             }
         }
     } else {
