@@ -78,3 +78,28 @@ def test_out_of_range_queries():
     assert r.cpu().numpy().view(np.uint64).tolist() == [2**64 - 1] * 2
     s = idx.select(sym, torch.tensor([1, 0], dtype=torch.int64, device="cuda"))
     assert s.cpu().numpy().view(np.uint64).tolist() == [2**64 - 1] * 2
+
+
+def test_matrix_queries_32_levels():
+    """The widest matrix (sigma = 2^32, 32 levels): access, rank and select against
+    direct counting, with symbols spread over the whole 32-bit range."""
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    rng = np.random.default_rng(32)
+    vals = rng.integers(0, 1 << 32, size=300, dtype=np.uint64).astype(np.uint32)
+    T = vals[rng.integers(0, vals.size, size=40000)]
+    n, sigma = T.size, 1 << 32
+    bv, z = wtg.wm_build(torch_text(T), sigma)
+    idx = wtg.WtIndex(wtg.WT_MATRIX, bv, n, sigma, z)
+    q = 2000
+    pos = rng.integers(0, n, size=q).astype(np.uint64)
+    sym = T[rng.integers(0, n, size=q)].astype(np.uint32)
+    jj = rng.integers(1, 300, size=q).astype(np.uint64)
+    acc, rank, sel = _brute(T, sigma, pos, sym, jj)
+    dpos = torch.from_numpy(pos.view(np.int64)).cuda()
+    dsym = torch.from_numpy(sym.view(np.int32)).cuda()
+    dj = torch.from_numpy(jj.view(np.int64)).cuda()
+    assert np.array_equal(idx.access(dpos).cpu().numpy().view(np.uint32), T[pos.astype(np.int64)])
+    assert np.array_equal(idx.rank(dsym, dpos).cpu().numpy().view(np.uint64), rank)
+    assert np.array_equal(idx.select(dsym, dj).cpu().numpy().view(np.uint64), sel)
