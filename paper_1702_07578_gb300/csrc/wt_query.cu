@@ -549,8 +549,10 @@ struct MapLayout {
     RsLayout wt;                  // the WT rank support this map is built from
     uint32_t L = 0;
     uint64_t ubits = 0, uW = 0, uNB = 0, unchunks = 0;
-    size_t off_u = 0, off_udir = 0, off_ucsum = 0, off_x = 0, bytes = 0;
+    size_t off_u = 0, off_udir = 0, off_ucsum = 0, off_x = 0, off_xsum = 0, bytes = 0;
 };
+
+constexpr uint32_t kXChunk = 4096;     // nodes per block of the X scan of a large level
 
 wt_status map_layout(uint64_t n, uint64_t sigma, MapLayout &m)
 {
@@ -570,6 +572,8 @@ wt_status map_layout(uint64_t n, uint64_t sigma, MapLayout &m)
     off = align256(off + 4 * m.unchunks);
     m.off_x = off;
     off = align256(off + 4 * (m.L >= 1 ? (1ull << m.L) : 1ull));
+    m.off_xsum = off;                  // chunk totals of the largest level's scan
+    off = align256(off + 4 * ((m.L >= 2 ? (1ull << (m.L - 1)) : 1ull) / kXChunk + 1));
     m.bytes = off;
     return WT_OK;
 }
@@ -615,24 +619,65 @@ __global__ void k_u_zeros(QArgs wt, uint64_t *u)
     atomicAnd(reinterpret_cast<unsigned long long *>(u + (z1 >> 6)), ~(1ull << (z1 & 63)));
 }
 
-// X for level l (one block): exclusive scan of the level's interval sizes in
-// bit-reversal order (Sec. 5.1); sizes from the WT node starts.
-__global__ void __launch_bounds__(1024) k_x_level(QArgs wt, uint32_t *X, uint32_t l)
+// X of level l: the exclusive scan of the level's interval sizes in bit-reversal
+// order (Sec. 5.1); sizes from the WT node starts.  Node r of the scan order is
+// p = rho_l(r); X[2^l - 2 + p] receives its start.  Levels with more than kXChunk
+// nodes are scanned by one block per chunk of the order: the chunk totals first
+// (pass 0), their scan, then the chunks with their carries (pass 1).
+__device__ __forceinline__ uint32_t x_size(const QArgs &wt, uint32_t l, uint64_t r)
+{
+    const uint32_t p = __brev((uint32_t)r) >> (32 - l);
+    const uint32_t *S = wt.S + tbl_off(l);
+    return S[p + 1] - S[p];
+}
+
+// chunk c of level l (kXChunk nodes, 4 per thread): totals (pass 0) or starts (pass 1)
+__global__ void __launch_bounds__(1024) k_x_chunks(QArgs wt, uint32_t *X, uint32_t *xsum, uint32_t l, uint32_t pass)
+{
+    __shared__ uint32_t ws[32];
+    const uint64_t cnt = 1ull << l, r0 = (uint64_t)blockIdx.x * kXChunk + 4ull * threadIdx.x;
+    uint32_t v[4], t = 0;
+    for (int j = 0; j < 4; ++j) {
+        v[j] = r0 + j < cnt ? x_size(wt, l, r0 + j) : 0u;
+        t += v[j];
+    }
+    uint32_t total;
+    uint32_t run = block_scan_1024(t, ws, &total);
+    if (pass == 0) {
+        if (threadIdx.x == 0) xsum[blockIdx.x] = total;
+        return;
+    }
+    run += xsum[blockIdx.x];
+    for (int j = 0; j < 4; ++j) {
+        if (r0 + j < cnt) X[cnt - 2 + (__brev((uint32_t)(r0 + j)) >> (32 - l))] = run;
+        run += v[j];
+    }
+}
+
+// one block: a whole small level (pass 0), or the exclusive scan of xsum (pass 1)
+__global__ void __launch_bounds__(1024) k_x_level(QArgs wt, uint32_t *X, uint32_t *xsum, uint32_t l, uint32_t nchunks)
 {
     __shared__ uint32_t ws[32];
     const uint64_t cnt = 1ull << l;
-    const uint32_t *S = wt.S + tbl_off(l);
-    uint32_t carry = 0;
-    for (uint64_t r0 = 0; r0 < cnt; r0 += 1024) {
-        const uint64_t r = r0 + threadIdx.x;
-        uint32_t sz = 0, p = 0;
-        if (r < cnt) {
-            p = __brev((uint32_t)r) >> (32 - l);
-            sz = S[p + 1] - S[p];
+    if (nchunks == 0) {
+        uint32_t carry = 0;
+        for (uint64_t r0 = 0; r0 < cnt; r0 += 1024) {
+            const uint64_t r = r0 + threadIdx.x;
+            const uint32_t sz = r < cnt ? x_size(wt, l, r) : 0u;
+            uint32_t total;
+            const uint32_t ex = block_scan_1024(sz, ws, &total);
+            if (r < cnt) X[cnt - 2 + (__brev((uint32_t)r) >> (32 - l))] = carry + ex;
+            carry += total;
         }
+        return;
+    }
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < nchunks; c0 += 1024) {
+        const uint32_t c = c0 + threadIdx.x;
+        const uint32_t v = c < nchunks ? xsum[c] : 0u;
         uint32_t total;
-        const uint32_t ex = block_scan_1024(sz, ws, &total);
-        if (r < cnt) X[cnt - 2 + p] = carry + ex;
+        const uint32_t ex = block_scan_1024(v, ws, &total);
+        if (c < nchunks) xsum[c] = carry + ex;
         carry += total;
     }
 }
@@ -689,7 +734,18 @@ wt_status wt_wt2wm_build(const uint64_t *d_bv, const void *d_rs, uint64_t n, uin
     k_dir_chunk_scan<<<1, 1024, 0, s>>>(u);
     k_dir_apply<<<grid, 1024, 0, s>>>(u);
     uint32_t *X = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(d_map) + m.off_x);
-    for (uint32_t l = 1; l < m.L; ++l) k_x_level<<<1, 1024, 0, s>>>(wt, X, l);
+    uint32_t *xsum = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(d_map) + m.off_xsum);
+    for (uint32_t l = 1; l < m.L; ++l) {
+        const uint64_t cnt = 1ull << l;
+        if (cnt <= kXChunk) {
+            k_x_level<<<1, 1024, 0, s>>>(wt, X, xsum, l, 0u);
+        } else {
+            const uint32_t chunks = (uint32_t)(cnt / kXChunk);
+            k_x_chunks<<<chunks, 1024, 0, s>>>(wt, X, xsum, l, 0u);
+            k_x_level<<<1, 1024, 0, s>>>(wt, X, xsum, l, chunks);
+            k_x_chunks<<<chunks, 1024, 0, s>>>(wt, X, xsum, l, 1u);
+        }
+    }
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 
