@@ -347,82 +347,63 @@ def run_ours(args):
                                for f, v in fprof.items()}}
         del ws_f, fb_t, fb_m, fz
 
-    # End to end through the C ABI with host buffers: every step copies its text
-    # from pinned host memory, builds both structures and copies both results back.
-    # Three streams (copy in, build, copy out) and three buffer sets let the copies
-    # of one step overlap the builds of the next two; the timed region runs from the
-    # first copy in to the last copy out.
+    # End to end through the C ABI with host buffers: every step is one
+    # wt_build_host call, which copies the text in from page-locked host memory,
+    # builds both structures (wt_build + wm_build, or wt_wm_build for the one-pass
+    # line) and copies both results back, all on its stream.  Steps go round-robin
+    # over three streams, each with its own device workspace and host outputs, so
+    # the copies of one step overlap the builds of the next; the timed region runs
+    # from before the first call to the end of the last copy out on every stream.
     pin = host.pin_memory()
     nsets = 3
-    sets = []
-    for b in range(nsets):
-        sets.append({
-            "text": text if b == 0 else torch.empty_like(text),
-            "bv_t": bv_t if b == 0 else torch.empty_like(bv_t),
-            "bv_m": bv_m if b == 0 else torch.empty_like(bv_m),
-            "z": z if b == 0 else torch.empty_like(z),
-            "out_t": torch.empty((L, W), dtype=torch.int64).pin_memory(),
-            "out_m": torch.empty((L, W), dtype=torch.int64).pin_memory(),
-            "out_z": torch.empty((max(L, 1),), dtype=torch.int64).pin_memory(),
-            "ev_in": torch.cuda.Event(), "ev_built": torch.cuda.Event(), "ev_out": torch.cuda.Event(),
-        })
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    s_build = torch.cuda.Stream()
-    for st in sets:                       # all buffers start free
-        st["ev_built"].record(s_build)
-        st["ev_out"].record(s_out)
+    hws = wtg.wt_host_workspace_size(w, n, sigma)
+    sets = [{"stream": torch.cuda.Stream(),
+             "ws": torch.empty((hws,), dtype=torch.uint8, device="cuda"),
+             "out_t": torch.empty((L, W), dtype=torch.int64).pin_memory(),
+             "out_m": torch.empty((L, W), dtype=torch.int64).pin_memory(),
+             "out_z": torch.empty((max(L, 1),), dtype=torch.int64).pin_memory()} for _ in range(nsets)]
     e2e_steps = max(3, args.steps)
 
-    use_fused = [False]
-    ws_e2e_f = torch.empty((wtg.wt_wm_workspace_size(w, n, sigma),), dtype=torch.uint8, device="cuda") \
-        if fused is not None else None
-
-    def e2e_step(i):
+    def e2e_step(i, one_pass):
         st = sets[i % nsets]
-        s_in.wait_event(st["ev_built"])   # the previous build that read this text is done
-        with torch.cuda.stream(s_in):
-            st["text"].copy_(pin, non_blocking=True)
-            st["ev_in"].record(s_in)
-        s_build.wait_event(st["ev_in"])
-        s_build.wait_event(st["ev_out"])  # the previous results of this set are copied out
-        if use_fused[0]:
-            wtg.wt_wm_build(st["text"], sigma, bv_wt=st["bv_t"], bv_wm=st["bv_m"], zeros=st["z"], ws=ws_e2e_f,
-                            stream=s_build)
-        else:
-            wtg.wt_build(st["text"], sigma, bv=st["bv_t"], ws=ws_t, stream=s_build)
-            wtg.wm_build(st["text"], sigma, bv=st["bv_m"], zeros=st["z"], ws=ws_m, stream=s_build)
-        st["ev_built"].record(s_build)
-        s_out.wait_event(st["ev_built"])
-        with torch.cuda.stream(s_out):
-            st["out_t"].copy_(st["bv_t"], non_blocking=True)
-            st["out_m"].copy_(st["bv_m"], non_blocking=True)
-            st["out_z"].copy_(st["z"], non_blocking=True)
-            st["ev_out"].record(s_out)
+        wtg.wt_build_host(pin, sigma, one_pass=one_pass, out_wt=st["out_t"], out_wm=st["out_m"],
+                          out_zeros=st["out_z"], ws=st["ws"], stream=st["stream"])
 
-    def e2e_run():
+    def e2e_run(one_pass):
         for i in range(nsets):
-            e2e_step(i)
+            e2e_step(i, one_pass)
+        for st in sets:
+            wtg.wt_sync_status(st["ws"], stream=st["stream"])
         torch.cuda.synchronize()
         barrier(pg)
+        cur = torch.cuda.current_stream()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(s_in)
+        f0.record(cur)
+        for st in sets:
+            st["stream"].wait_stream(cur)
         for i in range(e2e_steps):
-            e2e_step(i)
-        f1.record(s_out)
+            e2e_step(i, one_pass)
+        for st in sets:
+            cur.wait_stream(st["stream"])
+        f1.record(cur)
         torch.cuda.synchronize()
-        assert torch.equal(sets[(e2e_steps - 1) % nsets]["out_t"], bv_t.cpu())
+        last = sets[(e2e_steps - 1) % nsets]
+        assert torch.equal(last["out_t"], bv_t.cpu()) and torch.equal(last["out_m"], bv_m.cpu())
         return max_over_ranks(pg, f0.elapsed_time(f1) / e2e_steps)
 
-    e2e_ms = e2e_run()
-    if fused is not None:                 # the same pipeline with one wt_wm_build per step
-        use_fused[0] = True
-        f_e2e_ms = e2e_run()
+    e2e_ms = e2e_run(False)
+    d2h = 2 * L * W * 8 + L * 8
+    if fused is not None:                 # the same pipeline, both structures from one pass
+        f_e2e_ms = e2e_run(True)
         fused["e2e"] = {"value": world * 2 * n / (f_e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * w,
-                        "d2h_bytes_per_step": 2 * L * W * 8 + max(L, 1) * 8, "ms_per_step": f_e2e_ms}
+                        "d2h_bytes_per_step": d2h, "ms_per_step": f_e2e_ms,
+                        "call": "wt_build_host(one_pass=1)"}
     e2e = {"value": world * 2 * n / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * w,
-           "d2h_bytes_per_step": 2 * L * W * 8 + max(L, 1) * 8, "ms_per_step": e2e_ms,
-           "pipelining": "copy-in, build and copy-out of consecutive steps overlap (3 streams, 3 buffer sets)"}
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+           "call": "wt_build_host (host text in; wt_build + wm_build; both levels and Z out)",
+           "pipelining": "one call per step, round-robin over 3 streams with their own workspaces and outputs"}
+    del sets
 
     if rank != 0:
         return 0

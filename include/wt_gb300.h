@@ -148,6 +148,30 @@ wt_status wt_wm_workspace_size(wt_symtype type, uint64_t n, uint64_t sigma, size
 wt_status wt_wm_build(const void *d_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *d_bv_wt,
                       uint64_t *d_bv_wm, uint64_t *d_zeros, void *d_ws, size_t ws_bytes, void *stream);
 
+/* ---- host buffers in, host buffers out ----------------------------------------
+ * The problem of Sec. 2 with the text and the levels in host memory.  On `stream`
+ * the call copies the text into the device workspace, builds the WT
+ * (h_bv_wt != NULL) and/or the WM (h_bv_wm != NULL), and copies the levels
+ * (L * W words each, the layout above) and, for the WM, Z[0..L) (h_zeros) back.
+ * The builds are wt_build and wm_build, or wt_wm_build (both from one pass)
+ * when both are asked for and one_pass != 0; the results are bit-identical.
+ *   h_text   n symbols of the given type (host memory; may be NULL when n = 0)
+ *   h_bv_wt  L * W words or NULL;  h_bv_wm  L * W words or NULL (not both NULL)
+ *   h_zeros  L words, required with h_bv_wm when L > 0
+ *   d_ws     device memory of ws_bytes >= wt_host_workspace_size(...): the
+ *            build workspace at offset 0 (so wt_sync_status(d_ws) reads the
+ *            builds' device-detected errors), then the device copy of the text
+ *            and the device levels of both kinds.
+ * The copies are cudaMemcpyAsync on `stream`: with page-locked host buffers the
+ * call returns before they finish (synchronise the stream, or call
+ * wt_sync_status, before reading or reusing the host buffers); with pageable
+ * buffers CUDA makes them synchronous for the host.  Argument errors are
+ * returned before anything is queued; limits are those of the builds. */
+wt_status wt_host_workspace_size(wt_symtype type, uint64_t n, uint64_t sigma, size_t *bytes);
+wt_status wt_build_host(const void *h_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *h_bv_wt,
+                        uint64_t *h_bv_wm, uint64_t *h_zeros, int one_pass, void *d_ws, size_t ws_bytes,
+                        void *stream);
+
 /* ---- wavelet tree without any device allocation --------------------------
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code running under a host

@@ -212,6 +212,54 @@ def wt_wm_build(text, sigma: int, bv_wt=None, bv_wm=None, zeros=None, ws=None, s
     return bv_wt, bv_wm, zeros[:L]
 
 
+_HOST_DUMMY = ctypes.c_uint64(0)      # stands for an empty host output (nothing is written to it)
+
+
+def _hptr(t):
+    """Host pointer of an output that is asked for, even when it has no elements."""
+    if t.numel() > 0:
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(ctypes.addressof(_HOST_DUMMY))
+
+
+def wt_host_workspace_size(symtype: int, n: int, sigma: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().wt_host_workspace_size(symtype, int(n), int(sigma), ctypes.byref(out)), "wt_host_workspace_size")
+    return out.value
+
+
+def wt_build_host(text, sigma: int, wt=True, wm=True, one_pass=False, out_wt=None, out_wm=None, out_zeros=None,
+                  ws=None, stream=None):
+    """Host text in, host levels out (wt_build_host): returns (WT bits or None, WM bits or None, Z or None).
+
+    text and the outputs are contiguous CPU tensors; page-locked ones make the
+    call asynchronous on `stream` (synchronise before reading them)."""
+    torch = _torch()
+    if text.is_cuda or not text.is_contiguous():
+        raise ValueError("text must be a contiguous CPU tensor")
+    if not (wt or wm):
+        raise ValueError("ask for the WT, the WM or both")
+    n = text.numel()
+    L = wt_levels(sigma)
+    W = wt_words_per_level(n)
+    pin = text.is_pinned()
+    if wt and out_wt is None:
+        out_wt = torch.empty((L, W), dtype=torch.int64, pin_memory=pin)
+    if wm and out_wm is None:
+        out_wm = torch.empty((L, W), dtype=torch.int64, pin_memory=pin)
+    if wm and out_zeros is None:
+        out_zeros = torch.empty((max(L, 1),), dtype=torch.int64, pin_memory=pin)
+    for o in (out_wt, out_wm, out_zeros):
+        if o is not None and (o.is_cuda or not o.is_contiguous()):
+            raise ValueError("outputs must be contiguous CPU tensors")
+    if ws is None:
+        ws = torch.empty((wt_host_workspace_size(_symtype(text), n, sigma),), dtype=torch.uint8, device="cuda")
+    _check(lib().wt_build_host(_ptr(text), _symtype(text), n, int(sigma), _hptr(out_wt) if wt else None,
+                               _hptr(out_wm) if wm else None, _hptr(out_zeros) if wm else None, 1 if one_pass else 0,
+                               _ptr(ws), ws.numel(), _stream(stream)), "wt_build_host")
+    return out_wt if wt else None, out_wm if wm else None, out_zeros[:L] if wm else None
+
+
 def wt_sync_status(ws, stream=None):
     """Synchronise and raise WtError if the device recorded an error in ws."""
     _check(lib().wt_sync_status(_ptr(ws), _stream(stream)), "device")

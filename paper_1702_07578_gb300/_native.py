@@ -177,6 +177,9 @@ SIGNATURES = {
     "wt_wm_workspace_size": (_C.c_int, [_C.c_int, _C.c_uint64, _C.c_uint64, _C.POINTER(_C.c_size_t)]),
     "wt_wm_build": (_C.c_int, [_C.c_void_p, _C.c_int, _C.c_uint64, _C.c_uint64, _C.c_void_p, _C.c_void_p,
                                _C.c_void_p, _C.c_void_p, _C.c_size_t, _C.c_void_p]),
+    "wt_host_workspace_size": (_C.c_int, [_C.c_int, _C.c_uint64, _C.c_uint64, _C.POINTER(_C.c_size_t)]),
+    "wt_build_host": (_C.c_int, [_C.c_void_p, _C.c_int, _C.c_uint64, _C.c_uint64, _C.c_void_p, _C.c_void_p,
+                                 _C.c_void_p, _C.c_int, _C.c_void_p, _C.c_size_t, _C.c_void_p]),
     "wt_wt2wm_size": (_C.c_int, [_C.c_uint64, _C.c_uint64, _C.POINTER(_C.c_size_t)]),
     "wt_wt2wm_build": (_C.c_int, [_C.c_void_p, _C.c_void_p, _C.c_uint64, _C.c_uint64, _C.c_void_p,
                                   _C.c_size_t, _C.c_void_p]),

@@ -1,5 +1,6 @@
 // C ABI of wt_gb300: argument checks, workspace planning and round launches
 // for wt_build / wm_build / wt_build_batched.  See include/wt_gb300.h.
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -441,6 +442,90 @@ wt_status wm_build_order(const void *d_text, wt_symtype type, uint64_t n, uint64
 {
     return build_order(WT_MATRIX, d_text, type, n, sigma, d_bv, d_zeros, d_perm, d_sorted, d_ws, ws_bytes,
                        stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device workspace of wt_build_host: the build workspace (the largest of the WT,
+// WM and one-pass builds) at offset 0, then the text, the WT and WM levels and Z.
+struct HostLayout {
+    size_t text = 0, bv_wt = 0, bv_wm = 0, zeros = 0, bytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+wt_status host_layout(wt_symtype type, uint64_t n, uint64_t sigma, HostLayout &h)
+{
+    size_t a = 0, b = 0, c = 0;
+    wt_status st = wt_workspace_size(WT_MATRIX, type, n, sigma, &b);
+    if (st != WT_OK) return st;
+    if (wt_workspace_size(WT_TREE, type, n, sigma, &a) != WT_OK) a = 0;    // alphabet beyond the WT's limit
+    if (wt_wm_workspace_size(type, n, sigma, &c) != WT_OK) c = 0;
+    const uint64_t L = levels_of(sigma), W = (n + 63) / 64;
+    size_t off = align256(std::max(a, std::max(b, c)));
+    h.text = off;
+    off = align256(off + (size_t)n * (uint32_t)type);
+    h.bv_wt = off;
+    off = align256(off + (size_t)(L * W * 8));
+    h.bv_wm = off;
+    off = align256(off + (size_t)(L * W * 8));
+    h.zeros = off;
+    h.bytes = align256(off + 8 * (size_t)(L ? L : 1));
+    return WT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wt_status wt_host_workspace_size(wt_symtype type, uint64_t n, uint64_t sigma, size_t *bytes)
+{
+    if (bytes == nullptr) return WT_ERR_INVALID_ARG;
+    HostLayout h;
+    wt_status st = host_layout(type, n, sigma, h);
+    if (st == WT_OK) *bytes = h.bytes;
+    return st;
+}
+
+wt_status wt_build_host(const void *h_text, wt_symtype type, uint64_t n, uint64_t sigma, uint64_t *h_bv_wt,
+                        uint64_t *h_bv_wm, uint64_t *h_zeros, int one_pass, void *d_ws, size_t ws_bytes,
+                        void *stream)
+{
+    if (d_ws == nullptr || (h_bv_wt == nullptr && h_bv_wm == nullptr)) return WT_ERR_INVALID_ARG;
+    HostLayout h;
+    wt_status st = host_layout(type, n, sigma, h);
+    if (st != WT_OK) return st;
+    if (ws_bytes < h.bytes) return WT_ERR_OUT_OF_MEMORY;
+    const uint64_t L = levels_of(sigma), W = (n + 63) / 64;
+    if (n > 0 && h_text == nullptr) return WT_ERR_INVALID_ARG;
+    if (h_bv_wm != nullptr && L > 0 && h_zeros == nullptr) return WT_ERR_INVALID_ARG;
+    if (h_bv_wt != nullptr && sigma > (1ull << 24)) return WT_ERR_INVALID_ARG;
+    uint8_t *base = static_cast<uint8_t *>(d_ws);
+    void *d_text = base + h.text;
+    uint64_t *d_bv_wt = reinterpret_cast<uint64_t *>(base + h.bv_wt);
+    uint64_t *d_bv_wm = reinterpret_cast<uint64_t *>(base + h.bv_wm);
+    uint64_t *d_zeros = reinterpret_cast<uint64_t *>(base + h.zeros);
+    const size_t bws = h.text;                   // the build workspace ends where the text starts
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n > 0 && cudaMemcpyAsync(d_text, h_text, (size_t)n * (uint32_t)type, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return WT_ERR_CUDA;
+    if (h_bv_wt != nullptr && h_bv_wm != nullptr && one_pass) {
+        st = wt_wm_build(d_text, type, n, sigma, d_bv_wt, d_bv_wm, d_zeros, d_ws, bws, stream);
+    } else {
+        if (h_bv_wt != nullptr) st = wt_build(d_text, type, n, sigma, d_bv_wt, d_ws, bws, stream);
+        if (st == WT_OK && h_bv_wm != nullptr) st = wm_build(d_text, type, n, sigma, d_bv_wm, d_zeros, d_ws, bws, stream);
+    }
+    if (st != WT_OK) return st;
+    const size_t lvl = (size_t)(L * W * 8);
+    if (lvl > 0 && h_bv_wt != nullptr && cudaMemcpyAsync(h_bv_wt, d_bv_wt, lvl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return WT_ERR_CUDA;
+    if (lvl > 0 && h_bv_wm != nullptr && cudaMemcpyAsync(h_bv_wm, d_bv_wm, lvl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return WT_ERR_CUDA;
+    if (L > 0 && h_bv_wm != nullptr && cudaMemcpyAsync(h_zeros, d_zeros, 8 * L, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return WT_ERR_CUDA;
+    return WT_OK;
 }
 
 }  // extern "C"
