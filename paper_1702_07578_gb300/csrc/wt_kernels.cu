@@ -552,6 +552,16 @@ __device__ __forceinline__ uint64_t extract_bits(const uint32_t *lvl, uint32_t p
     return r;
 }
 
+// k (1..64) bits of a tile's level plane starting at bit p (p + k <= kBsTile; the
+// plane has two spare words past its end, so the third word read stays inside).
+__device__ __forceinline__ uint64_t run_bits(const uint32_t *lvl, uint32_t p, uint32_t k)
+{
+    const uint32_t w = p >> 5, s = p & 31u;
+    const uint32_t a = lvl[w], b = lvl[w + 1], c = lvl[w + 2];
+    const uint64_t r = ((uint64_t)__funnelshift_r(b, c, s) << 32) | __funnelshift_r(a, b, s);
+    return k < 64 ? r & ((1ull << k) - 1ull) : r;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -622,22 +632,41 @@ __device__ __forceinline__ uint32_t shr_hi(uint32_t x, uint32_t s)
 }
 
 // Masks of compress(., m) (Hacker's Delight, Sec. 7-4): in round i (i = 0..4)
-// bits travel 2^i places towards bit 0; mv[i] holds the positions they arrive at.
-__device__ __forceinline__ void compress_moves(uint32_t m, uint32_t mv[5])
+// bits travel 2^i places towards bit 0; the receive mask of round i holds the
+// positions they arrive at.  The bits that move in round i are those under a one of
+// the prefix XOR of the positions above a zero of m (after the earlier rounds).
+// Both mask sets of a word: compress(., ~m) (zeros) and compress(., m) (ones).
+// Round 0 of the second set reuses the first's prefix XOR: the two start masks
+// differ by 0xFFFFFFFE (all bits but bit 0) and the prefix XOR is linear, so their
+// prefix XORs differ by the prefix XOR of 0xFFFFFFFE, 0xAAAAAAAA.
+__device__ __forceinline__ void compress_moves_split(uint32_t m, uint32_t mz[5], uint32_t mo[5])
 {
-    uint32_t mk = mul_lo(~m, 2u);
+    uint32_t kz = mul_lo(m, 2u), ko = mul_lo(~m, 2u), az = ~m, ao = m;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        uint32_t mp = mk ^ mul_lo(mk, 2u);
-        mp ^= mul_lo(mp, 4u);
-        mp ^= mul_lo(mp, 16u);
-        mp ^= mul_lo(mp, 256u);
-        mp ^= mul_lo(mp, 65536u);
-        const uint32_t v = mp & m;
-        const uint32_t vs = shr_hi(v, 1u << i);
-        m = (m ^ v) | vs;
-        mv[i] = vs;                 // receive mask of round i: positions a bit arrives at
-        mk &= ~mp;
+        uint32_t pz = kz ^ mul_lo(kz, 2u);
+        pz ^= mul_lo(pz, 4u);
+        pz ^= mul_lo(pz, 16u);
+        pz ^= mul_lo(pz, 256u);
+        pz ^= mul_lo(pz, 65536u);
+        uint32_t po;
+        if (i == 0) {
+            po = pz ^ 0xAAAAAAAAu;
+        } else {
+            po = ko ^ mul_lo(ko, 2u);
+            po ^= mul_lo(po, 4u);
+            po ^= mul_lo(po, 16u);
+            po ^= mul_lo(po, 256u);
+            po ^= mul_lo(po, 65536u);
+        }
+        const uint32_t vz = pz & az, vo = po & ao;
+        const uint32_t sz = shr_hi(vz, 1u << i), so = shr_hi(vo, 1u << i);
+        az = (az ^ vz) | sz;
+        ao = (ao ^ vo) | so;
+        mz[i] = sz;
+        mo[i] = so;
+        kz &= ~pz;
+        ko &= ~po;
     }
 }
 
@@ -947,15 +976,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 const uint32_t *wpre = out ? sm.wpre2 : sm.wpre;
                 uint64_t *lv = (out ? t.bv2 : t.bv) + (uint64_t)(rt.c + l) * t.W;
                 for (uint32_t k = tid; k < wt; k += kThreads) {
+                    // word `rel` of the class's run; positions relative to bit 0 of
+                    // that word fit in 32 bits (a run has at most kBsTile bits)
                     const uint32_t idx = base + wc[k];
-                    const uint64_t gs = glo[idx], ge = gs + sm.cnt[idx];
-                    const uint64_t word = (gs >> 6) + (k - wpre[idx]);
-                    const uint64_t wb = word << 6;
-                    const uint32_t blo = (uint32_t)((gs > wb ? gs : wb) - wb);
-                    uint32_t bhi = (uint32_t)((ge < wb + 64 ? ge : wb + 64) - wb);
-                    const uint32_t src = sm.loc[idx] + (uint32_t)(wb + blo - gs);
-                    const uint64_t val = extract_bits(sm.lvl, src, bhi - blo) << blo;
-                    if (ge == t.n) bhi = 64;       // bits past n belong to the last interval
+                    const uint32_t gs = glo[idx], c = sm.cnt[idx];
+                    const uint32_t rel = k - wpre[idx], g0 = gs & 63u;
+                    const uint32_t blo = rel ? 0u : g0;
+                    uint32_t bhi = min(c + g0 - 64u * rel, 64u);
+                    const uint32_t src = sm.loc[idx] + 64u * rel + blo - g0;
+                    const uint64_t val = run_bits(sm.lvl, src, bhi - blo) << blo;
+                    const uint64_t word = (uint64_t)(gs >> 6) + rel;
+                    if ((uint64_t)gs + c == t.n) bhi = 64;   // bits past n belong to the last interval
                     if (blo == 0 && bhi == 64) {
                         lv[word] = val;
                     } else {
@@ -969,10 +1000,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             // stable split of every later plane by plane l
             if (l + 1 < h) {
                 uint32_t mz0[5], mo0[5], mz1[5], mo1[5];
-                compress_moves(~m0, mz0);
-                compress_moves(m0, mo0);
-                compress_moves(~m1, mz1);
-                compress_moves(m1, mo1);
+                compress_moves_split(m0, mz0, mo0);
+                compress_moves_split(m1, mz1, mo1);
                 const uint32_t dz = zo, d1 = zt + w0 * 32u - zo;
                 const uint32_t nz = z0 + z1, no = 64u - nz;
                 const uint32_t kz0 = z0 == 32u ? ~0u : (1u << z0) - 1u;
@@ -1298,8 +1327,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
                 const uint32_t wj = 32u * j + lane;
                 const uint32_t m0 = mw[j], z0 = zw[j], zo = zb[j];
                 uint32_t mz[5], mo[5];
-                compress_moves(~m0, mz);
-                compress_moves(m0, mo);
+                compress_moves_split(m0, mz, mo);
                 const uint32_t kz = z0 == 32u ? ~0u : (1u << z0) - 1u;
                 const uint32_t ko = z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u;
                 const uint32_t d1 = zt + 32u * wj - zo;
