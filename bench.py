@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (profiles/k_build_bs_bytes_n2e28_full.md)
-    "b38380557545bd8a36370d21ee28e7d21a26f8e5eaf5d6bdab05a6f2a602428d": {"dram_bytes": 344877568 + 222808320,
+    "ae02559e0eb50764d1ad49e336c3c2e063b1db5b6c91ba680be894280da49738": {"dram_bytes": 344706816 + 222797568,
                                                                          "n": 1 << 28},
 }
 
