@@ -58,3 +58,27 @@ def test_host_only_calls():
 def test_compiled_for_sm103a_only():
     """The build uses exactly one -gencode, for sm_103a."""
     assert _native.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
+
+
+def test_host_build_argument_errors():
+    """wt_build_host rejects bad arguments before it touches the device."""
+    lib = wtg.lib()
+    n, sigma = 100000, 256
+    need = wtg.wt_host_workspace_size(wtg.WT_U8, n, sigma)
+    text_bytes = n
+    levels = 8 * ((n + 63) // 64) * 8
+    # the build workspace, the text, two sets of levels and Z, each 256-byte aligned
+    assert need >= wtg.wt_wm_workspace_size(wtg.WT_U8, n, sigma) + text_bytes + 2 * levels + 64
+    assert wtg.wt_host_workspace_size(wtg.WT_U32, n, 1 << 25) > 0      # the WM alone may be asked for
+    buf = (ctypes.c_uint8 * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    fake_ws = ctypes.c_void_p(1 << 40)        # never dereferenced: every call below fails first
+    call = lib.wt_build_host
+    assert call(p, wtg.WT_U8, n, sigma, None, None, None, 0, fake_ws, need, None) == 1     # no output
+    assert call(p, wtg.WT_U8, n, sigma, p, None, None, 0, None, need, None) == 1           # no workspace
+    assert call(p, wtg.WT_U8, n, sigma, p, None, None, 0, fake_ws, need - 1, None) == 3    # workspace short
+    assert call(None, wtg.WT_U8, n, sigma, p, None, None, 0, fake_ws, need, None) == 1     # no text
+    assert call(p, wtg.WT_U8, n, sigma, None, p, None, 0, fake_ws, need, None) == 1        # WM without Z
+    assert call(p, wtg.WT_U8, n, 300, p, None, None, 0, fake_ws, need, None) == 1          # sigma > 2^8
+    big = wtg.wt_host_workspace_size(wtg.WT_U32, n, 1 << 25)
+    assert call(p, wtg.WT_U32, n, 1 << 25, p, None, None, 0, fake_ws, big, None) == 1      # WT beyond 2^24
