@@ -93,17 +93,12 @@ __device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uin
     return n > 0 && n <= kSmallJob && t.L - round_first_level(t.L, round) <= (uint32_t)kChunk && t.perm == nullptr;
 }
 
-// Lanes whose 8-bit key equals this lane's, among the lanes with ok set: the AND
-// of eight bit ballots (a warp multisplit), all lanes taking part.
-__device__ __forceinline__ uint32_t peers8(uint32_t key, bool ok)
+// Lanes whose key (< 2^8) equals this lane's, among the lanes with ok set, all
+// lanes taking part: one warp match (lanes without a key all carry 0xffffffff,
+// which no key equals).  Measured faster than the AND of eight bit ballots.
+__device__ __forceinline__ uint32_t class_peers(uint32_t key, bool ok)
 {
-    uint32_t peers = __ballot_sync(0xffffffffu, ok);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t b = __ballot_sync(0xffffffffu, (key >> k) & 1u);
-        peers &= ((key >> k) & 1u) ? b : ~b;
-    }
-    return peers;
+    return __match_any_sync(kFull, ok ? key : 0xffffffffu);
 }
 
 // The slot owning group g: the last slot whose first group is <= g (slots are
@@ -1102,7 +1097,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     const bool ok = e < e_end;
                     const uint32_t v = vs[k];
                     const uint32_t q = ok ? (v >> shift) & cmask : 0u;
-                    const uint32_t peers = peers8(q, ok);
+                    const uint32_t peers = class_peers(q, ok);
                     const uint32_t rank = ok ? cw[q] + __popc(peers & lt) : 0u;
                     __syncwarp();
                     if (ok) {
