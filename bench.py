@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (profiles/k_build_bs_bytes_n2e28_full.md)
-    "ae02559e0eb50764d1ad49e336c3c2e063b1db5b6c91ba680be894280da49738": {"dram_bytes": 344706816 + 222797568,
+    "fd242d804e1e1d3e690708483c2c46a32c9d6ca8a54d7e1bf563056d2b6b247a": {"dram_bytes": 344705280 + 222975488,
                                                                          "n": 1 << 28},
 }
 
