@@ -318,7 +318,10 @@ wt_status wt_server_read(wt_server *s, uint64_t ticket, uint64_t *h_bv, uint64_t
 /* Free the request's device memory; the ticket becomes invalid. */
 wt_status wt_server_release(wt_server *s, uint64_t ticket);
 wt_status wt_server_get_stats(wt_server *s, wt_server_stats *st);
-/* Finish in-flight work, free everything. */
+/* Let the batches already launched finish, drop the requests not launched yet
+ * (queued, or admitted and waiting for a stream), and free everything: every
+ * ticket of the server is invalid afterwards.  No other call on the server may
+ * run at the same time or later. */
 void wt_server_destroy(wt_server *s);
 
 /* ---- queries: access / rank / select on built bit vectors ---------------------

@@ -189,6 +189,19 @@ void scheduler(wt_server *s)
     for (;;) {
         for (Batch *b : s->finished) finish_batch(s, b);
         s->finished.clear();
+        if (s->stop) {
+            // destroy: requests not on a stream yet are dropped (pending ones might
+            // never be admitted: finished results keep their memory charged until
+            // released); batches already launched run to their callbacks
+            for (auto &r : s->admitted) s->in_use -= r->reserved;
+            s->admitted.clear();
+            s->pending.clear();
+            bool idle = true;
+            for (auto &sl : s->slots) idle &= !sl.busy;
+            if (idle) break;
+            s->cv_sched.wait(lk);
+            continue;
+        }
         // admission in arrival order
         while (!s->pending.empty()) {
             auto &r = s->pending.front();
@@ -214,11 +227,8 @@ void scheduler(wt_server *s)
             lk.lock();
             launched = true;
         }
-        if (s->stop && s->pending.empty() && s->admitted.empty()) {
-            bool idle = true;
-            for (auto &sl : s->slots) idle &= !sl.busy;
-            if (idle && s->finished.empty()) break;
-        }
+        // (stop is set under the lock: if nothing was launched, the lock was held
+        // since the check above and the next wake-up sees it)
         if (!launched) s->cv_sched.wait(lk);
     }
 }
