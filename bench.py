@@ -219,10 +219,15 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     per = statistics.median(times)
     v = 2 * S.size / per
+    w = T.dtype.itemsize
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference",
+        "metric": METRIC if args.workload == "bytes" and args.n_log2 is None
+        else f"input symbols/s, WT+WM construction ({desc})",
+        "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8" if w == 1 else f"u{8 * w}",
         "data": "synthetic", "config": {"workload": desc, "sample": f"first 2^{k} symbols"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"first 2^{k} symbols per step, WT + WM, 1 thread"},
@@ -870,7 +875,7 @@ def run_queries(args):
     return 0
 
 
-def main():
+def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -894,7 +899,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per k_build launch from an ncu capture (reported as is)")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
