@@ -261,9 +261,11 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
         a.gelems = p.gelems[r];
         a.groups_ub = p.groups_ub[r];
         a.blocks_ub = p.blocks_ub[r];
+        a.all_h8 = 1;
         for (uint32_t i = 0; i < p.count; ++i) {
             const TextInfo &ti = p.texts[i];
             if (ti.nslots[r] == 0) continue;
+            if (round_levels(ti.L, r) != (uint32_t)kChunk) a.all_h8 = 0;
             const bool last = r + 1 == round_count(ti.L);
             if (!last) a.any_cut = 1; else a.any_plain = 1;
             if (ti.perm != nullptr) a.any_order = 1;

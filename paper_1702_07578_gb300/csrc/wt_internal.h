@@ -35,8 +35,9 @@ constexpr int kTileSyms = 32768;      // symbols per tile of the bit-sliced buil
 constexpr uint32_t kBoth = 2;
 constexpr uint32_t kSmallJob = 4096;  // jobs of the last round up to this size: one warp each
 
-// Default symbols per build block: two tiles.
-constexpr uint32_t kDefaultGroup = 2 * 32768;
+// Default symbols per build block: four tiles (a block finishes the words that its
+// tiles' runs share, so fewer blocks means fewer words updated in place).
+constexpr uint32_t kDefaultGroup = 4 * 32768;
 
 // Round geometry.  A text of L levels is built in ceil(L / 8) rounds; the first
 // takes the L mod 8 top levels (8 when L is a multiple of 8) and every later round
@@ -113,6 +114,7 @@ struct RoundArgs {
     uint32_t any_plain;      // some job of the round has no cut (its text's last round)
     uint32_t any_order;      // some text of the round wants its stable order (perm)
     uint32_t any_small;      // some job of the round may be small (one warp each)
+    uint32_t all_h8;         // every job of the round splits 8 levels
     uint32_t *cscan;         // [2 * chunks]: group and tile totals per 4096 slots (many-slot rounds)
 };
 

@@ -574,12 +574,16 @@ namespace {
 
 constexpr int kBsWords = 2 * kThreads;        // words per plane
 constexpr int kBsTile = kBsWords * 32;        // 32768 symbols per tile
+constexpr int kRangeBits = 64 * 32;           // positions of one warp's words (2048)
 static_assert(kBsTile == kTileSyms, "tile histograms are written per kTileSyms symbols");
+static_assert(kRangeBits * kWarps == kBsTile, "each warp owns one range of the tile");
 
 struct BsSmem {
     uint32_t plane[2][kChunk][kBsWords + 2];  // current / next planes (+ overflow words)
-    uint32_t lvl[kBsWords + 4];               // the current level's plane, tile order
-    uint32_t wsum[kWarps];                    // zeros of each warp's range
+    uint64_t pend[2][kCols];                  // per level and class: bits of the group's earlier tiles in
+                                              // the word the class's run goes on in (tile parity)
+    uint32_t gst[kCols];                      // per level and class: the group's first bit in the level
+    uint32_t wz[kChunk][kWarps];              // zeros of level l's plane in each warp's range
     uint32_t thc[kCols];                      // class counts of the tile (histogram pass)
     union {
         uint16_t cntw[kWarps][kCols];         // cut: class counts / offsets per warp chunk
@@ -623,6 +627,22 @@ __device__ __forceinline__ uint32_t shr_hi(uint32_t x, uint32_t s)
 {
     uint32_t r;
     asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(1u << (32 - s)));
+    return r;
+}
+
+// high word of x * c
+__device__ __forceinline__ uint32_t mul_hi(uint32_t x, uint32_t c)
+{
+    uint32_t r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(c));
+    return r;
+}
+
+// x * c + a (low word)
+__device__ __forceinline__ uint32_t mad_lo(uint32_t x, uint32_t c, uint32_t a)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(c), "r"(a));
     return r;
 }
 
@@ -678,6 +698,88 @@ __device__ __forceinline__ uint32_t compress_apply(uint32_t x, uint32_t keep, co
     return x & keep;
 }
 
+// The same compress done inside each byte of a word at once, for the tile's
+// splits.  Three rounds move bits 1, 2 and 4 places towards bit 0 of their byte
+// (the moves never leave the byte: a selected bit moves by the number of
+// unselected bits below it in its byte); afterwards byte b holds its c_b selected
+// bits in its low c_b bits.  A join then puts byte b's run at bit c_0 + .. +
+// c_(b-1) of the word, with multiplies (below).  Per word and level this costs far
+// fewer operations for the masks than the five-round compress of a whole word,
+// whose move masks depend on prefix XORs across all 32 positions.
+struct ByteSplit {
+    uint32_t rz[3], ro[3];      // receive masks of rounds 0..2: zeros side, ones side
+    uint32_t kz, ko;            // selected bits after the rounds: the low c_b bits of each byte
+    uint32_t jz[3], jo[3];      // join multipliers (byte_join)
+};
+
+// prefix XOR inside every byte, from bit 0 up
+__device__ __forceinline__ uint32_t pxor8(uint32_t k)
+{
+    uint32_t p = k ^ (mul_lo(k, 2u) & 0xFEFEFEFEu);
+    p ^= mul_lo(p, 4u) & 0xFCFCFCFCu;
+    p ^= mul_lo(p, 16u) & 0xF0F0F0F0u;
+    return p;
+}
+
+// Join multipliers of a kept word whose byte b holds c_b bits (keep has the low c_b
+// bits of byte b set).  With M_b = 2^(c_0 + .. + c_(b-1)), byte b must be multiplied
+// by M_b; written as x + (x >> 8) K1 + (x >> 16) K2 + (x >> 24) K3 this holds for
+// K1 = M1 - 2^8, K2 = M2 - 2^8 M1, K3 = M3 - 2^8 M2 (all modulo 2^32).
+__device__ __forceinline__ void join_consts(uint32_t keep, uint32_t j[3])
+{
+    const uint32_t M1 = 1u << __popc(keep & 0xFFu);
+    const uint32_t M2 = 1u << __popc(keep & 0xFFFFu);
+    const uint32_t M3 = 1u << __popc(keep & 0xFFFFFFu);
+    j[0] = M1 - 256u;
+    j[1] = mad_lo(M1, 0xFFFFFF00u, M2);
+    j[2] = mad_lo(M2, 0xFFFFFF00u, M3);
+}
+
+// Byte-wise compress masks of a word for both sides (zeros of m, ones of m).
+// Round 0 of the ones side reuses the zeros side's prefix XOR: inside a byte the
+// two start masks differ by 0xFE and the prefix XOR is linear, so the prefix XORs
+// differ by that of 0xFE, 0xAA.
+__device__ __forceinline__ void byte_split(uint32_t m, ByteSplit &b)
+{
+    uint32_t kz = mul_lo(m, 2u) & 0xFEFEFEFEu;    // ones of m below, inside the byte
+    uint32_t ko = kz ^ 0xFEFEFEFEu;               // zeros of m below, inside the byte
+    uint32_t sz = ~m, so = m;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const uint32_t pz = pxor8(kz);
+        const uint32_t po = i == 0 ? pz ^ 0xAAAAAAAAu : pxor8(ko);
+        const uint32_t vz = pz & sz, vo = po & so;
+        const uint32_t rz = shr_hi(vz, 1u << i), ro = shr_hi(vo, 1u << i);
+        sz = (sz ^ vz) | rz;
+        so = (so ^ vo) | ro;
+        b.rz[i] = rz;
+        b.ro[i] = ro;
+        if (i < 2) {
+            kz &= ~pz;
+            ko &= ~po;
+        }
+    }
+    b.kz = sz;
+    b.ko = so;
+    join_consts(sz, b.jz);
+    join_consts(so, b.jo);
+}
+
+// compress of x inside its bytes (receive masks r, kept bits keep), then the
+// byte runs joined into one run from bit 0.  The rounds shift on the integer ALU,
+// the join multiplies on the multiply-add pipe, so that the two pipes share the
+// work of every plane split.
+__device__ __forceinline__ uint32_t byte_compress(uint32_t x, const uint32_t r[3], uint32_t keep, const uint32_t j[3])
+{
+    x = ((x >> 1) & r[0]) | (x & ~r[0]);
+    x = ((x >> 2) & r[1]) | (x & ~r[1]);
+    x = ((x >> 4) & r[2]) | (x & ~r[2]);
+    x &= keep;
+    uint32_t y = mad_lo(shr_hi(x, 8u), j[0], x);
+    y = mad_lo(shr_hi(x, 16u), j[1], y);
+    return mad_lo(shr_hi(x, 24u), j[2], y);
+}
+
 // OR the low `len` (<= 64) bits of `part` into a plane at bit offset d.
 __device__ __forceinline__ void place_bits(uint32_t *plane, uint32_t d, uint64_t part, uint32_t len)
 {
@@ -687,6 +789,58 @@ __device__ __forceinline__ void place_bits(uint32_t *plane, uint32_t d, uint64_t
     atomicOr(plane + w, (uint32_t)lo);
     if (s + len > 32u) atomicOr(plane + w + 1, (uint32_t)(lo >> 32));
     if (s + len > 64u) atomicOr(plane + w + 2, (uint32_t)(part >> (64u - s)));
+}
+
+// Where a thread's part of a split goes: its bit offset in the next plane, its
+// length, and the multipliers that spread it over the (up to three) words it
+// touches.  Shared by every plane split at one level.
+struct Dest {
+    uint32_t *row0;     // word of the first bit (in plane 0 of the buffer; add the plane's stride)
+    uint32_t ms;        // 2^(d mod 32)
+    uint32_t len;
+    bool w1, w2;        // the part reaches the second / third word
+};
+
+__device__ __forceinline__ Dest make_dest(uint32_t (*buf)[kBsWords + 2], uint32_t d, uint32_t len)
+{
+    Dest r;
+    const uint32_t s = d & 31u;
+    r.row0 = &buf[0][d >> 5];
+    r.ms = 1u << s;
+    r.len = len;
+    r.w1 = s + len > 32u;
+    r.w2 = s + len > 64u;
+    return r;
+}
+
+// OR the part (lo, hi: its low len bits) into plane k of the buffer.  The shift by
+// d mod 32 is done with multiplies (low and high words of part * 2^s).
+__device__ __forceinline__ void place_part(const Dest &d, uint32_t k, uint32_t lo, uint32_t hi)
+{
+    if (d.len == 0) return;
+    uint32_t *p = d.row0 + (size_t)k * (kBsWords + 2);
+    atomicOr(p, lo * d.ms);
+    if (d.w1) atomicOr(p + 1, mad_lo(hi, d.ms, mul_hi(lo, d.ms)));
+    if (d.w2) atomicOr(p + 2, mul_hi(hi, d.ms));
+}
+
+// Zeros of plane bits `part` (len bits at bit offset d of the next order) counted
+// into the two warp ranges the warp's run can touch: r0 (the range of the run's
+// first bit) and r0 + 1.  Returns the two counts of this thread.
+__device__ __forceinline__ void range_zeros(uint32_t d, uint32_t len, uint64_t part, uint32_t r0, uint32_t &a,
+                                            uint32_t &b)
+{
+    const uint32_t r = d / kRangeBits, room = kRangeBits - d % kRangeBits;
+    uint32_t za, zb = 0;
+    if (len <= room) {
+        za = len - __popcll(part);
+    } else {                                        // room < 64: the part ends in the next range
+        za = room - __popcll(part & ((1ull << room) - 1ull));
+        zb = (len - room) - __popcll(part >> room);
+    }
+    if (len == 0) za = 0;
+    if (r == r0) { a = za; b = zb; }
+    else { a = 0; b = za; }
 }
 
 // 8x8 bit transpose of the bytes of (lo, hi): afterwards byte j holds bit j of
@@ -754,28 +908,42 @@ __device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t
     }
 }
 
-// Transposes 32 symbols and stores plane k (code bit rb-1-k) of word w.
-__device__ __forceinline__ void store_planes(uint32_t x[8], uint32_t rb, uint32_t h,
-                                             uint32_t (*planes)[kBsWords + 2], uint32_t w)
+// Transposes 32 symbols and stores plane k (code bit rb-1-k) of word w; returns
+// plane 0's word.
+__device__ __forceinline__ uint32_t store_planes(uint32_t x[8], uint32_t rb, uint32_t h,
+                                                 uint32_t (*planes)[kBsWords + 2], uint32_t w)
 {
 #pragma unroll
     for (int b = 0; b < 4; ++b) transpose8(x[2 * b], x[2 * b + 1]);
+    uint32_t first = 0;
     for (uint32_t k = 0; k < h; ++k) {
         const uint32_t j = rb - 1u - k;               // bit position inside the byte
         const uint32_t sel = (j & 3u) | ((j & 3u) + 4u) << 4;
         const bool hi = j >= 4u;
         const uint32_t t01 = __byte_perm(hi ? x[1] : x[0], hi ? x[3] : x[2], sel);
         const uint32_t t23 = __byte_perm(hi ? x[5] : x[4], hi ? x[7] : x[6], sel);
-        planes[k][w] = __byte_perm(t01, t23, 0x5410);
+        const uint32_t v = __byte_perm(t01, t23, 0x5410);
+        planes[k][w] = v;
+        if (k == 0) first = v;
     }
+    return first;
 }
 
 }  // namespace
 
 // BOTH: kind kBoth (two sets of destinations).  CUT: the round runs the cut pass
 // (some job cuts, or some text wants its stable order); the plain build of texts
-// with sigma <= 256 is the instantiation without either.
-template <bool BOTH, bool CUT>
+// with sigma <= 256 is the instantiation without either.  H: the levels of every
+// job of the round when that is 8 (the loops over planes then have fixed bounds),
+// 0 for any number.
+//
+// One block barrier per level.  The zero offsets of level l need the zeros of
+// plane l in every warp's range of the tile; they are counted while plane l is
+// placed at level l - 1 (each warp adds its parts' zeros per destination range),
+// so a level starts right after the previous level's barrier.  Level l's bits are
+// copied out from plane l of the current buffer, which the level's splits leave
+// untouched.
+template <bool BOTH, bool CUT, int H>
 __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -788,7 +956,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const Job jb = a.jobs[slot];
     const TextInfo &t = a.texts[jb.text];
     const RoundText rt = round_text(t, a.round);
-    const uint32_t h = rt.h, rb = rt.rb;
+    const uint32_t h = H ? (uint32_t)H : rt.h, rb = rt.rb;
     const uint32_t shift = rb - h;                   // > 0 in rounds with a cut
     const uint32_t gi = g - jb.g0;
     const bool matrix = a.kind == WT_MATRIX;
@@ -838,9 +1006,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     uint32_t tix = 0;
     for (uint64_t t0 = g_begin; t0 < g_end; t0 += kBsTile, ++tix) {
         const uint32_t m = (uint32_t)min((uint64_t)kBsTile, g_end - t0);
-        // ---- class counts of the tile (from the histogram pass); clear the next-plane buffer
-        for (uint32_t i = tid; i < kChunk * (kBsWords + 2); i += kThreads) (&sm.plane[1][0][0])[i] = 0;
+        // ---- class counts of the tile (from the histogram pass); clear the next-plane
+        //      buffer and the zero counts of the levels after the first
+        {
+            uint4 *p1 = reinterpret_cast<uint4 *>(&sm.plane[1][0][0]);
+            constexpr uint32_t n4 = kChunk * (kBsWords + 2) / 4;
+            static_assert(kChunk * (kBsWords + 2) % 4 == 0, "plane buffer in 16-byte pieces");
+            for (uint32_t i = tid; i < n4; i += kThreads) p1[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
         if (tid < (uint32_t)kChunk) sm.plane[0][tid][kBsWords] = sm.plane[0][tid][kBsWords + 1] = 0;
+        if (tid < (uint32_t)(kChunk * kWarps)) (&sm.wz[0][0])[tid] = 0;
         for (uint32_t q = tid; q < kCols; q += kThreads)
             sm.thc[q] = a.thist[((size_t)tile_first + tix) * kCols + q];
         __syncthreads();
@@ -861,12 +1036,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint32_t l = 31u - __clz(idx), q = idx - (1u << l);
             if (l <= h) {
                 const uint32_t s = h - l, lo = q << s, hi = (q + 1) << s;
-                sm.cnt[idx] = sm.tP[hi] - sm.tP[lo];
-                sm.glo[idx] = jb.off + sm.jspos[idx] + (sm.oP[hi] - sm.oP[lo]);
+                const uint32_t c = sm.tP[hi] - sm.tP[lo], gs = jb.off + sm.jspos[idx] + (sm.oP[hi] - sm.oP[lo]);
+                sm.cnt[idx] = c;
+                sm.glo[idx] = gs;
                 if (both) sm.glo2[idx] = jb.off + sm.jspos2[idx] + (sm.oP[hi] - sm.oP[lo]);
+                if (!both && l < h) {                    // the group's runs (see the copy below)
+                    if (tix == 0) {
+                        sm.gst[idx] = gs;
+                        sm.pend[0][idx] = 0;
+                    } else if (c == 0) {
+                        const uint64_t v = sm.pend[(tix - 1) & 1][idx];
+                        sm.pend[tix & 1][idx] = v;
+                        // the group's last tile has no run of this class: the bits its
+                        // earlier tiles left in the word gs / 64 are written now
+                        if (t0 + kBsTile >= g_end && (gs & 63u) != 0) {
+                            const uint32_t gq = sm.gst[idx];
+                            const uint32_t lo = (gs >> 6) == (gq >> 6) ? (gq & 63u) : 0u;
+                            const uint64_t upto = (uint64_t)gs == t.n ? ~0ull : ((1ull << (gs & 63u)) - 1ull);
+                            const uint64_t msk = upto & ~((1ull << lo) - 1ull);   // bits past n belong to the last interval
+                            if (msk != 0) {
+                                unsigned long long *w = reinterpret_cast<unsigned long long *>(
+                                    t.bv + (uint64_t)(rt.c + l) * t.W + (gs >> 6));
+                                atomicAnd(w, ~msk);
+                                atomicOr(w, v);
+                            }
+                        }
+                    }
+                }
             }
         }
         __syncthreads();
+        // the leaf counts of this tile advance the job offsets for the next tile
+        // (oP, read above, is not needed again in this tile)
+        for (uint32_t q = tid; q < (1u << h); q += kThreads) sm.offq[q] += sm.cnt[(1u << h) + q];
         // per level (one warp each): class starts in tile order (reversed
         // prefixes, Obs. 2) and destination words of every class
         if (CUT && warp == h && (rt.cut != nullptr || t.perm != nullptr)) {   // class starts after the last split
@@ -920,25 +1122,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 wc[k] = (uint8_t)run;
             }
         }
-        // ---- load and transpose: plane k holds code bit rb-1-k of every symbol
+        // ---- the next tile of the group is fetched into L2 while this one is built
+        if (tid == 0 && t0 + kBsTile < g_end) {
+            const uintptr_t b = reinterpret_cast<uintptr_t>(in_base + (size_t)(t0 + kBsTile) * rt.in_w);
+            const uintptr_t e = reinterpret_cast<uintptr_t>(in_base + (size_t)min(g_end, t0 + 2 * (uint64_t)kBsTile) * rt.in_w);
+            const uintptr_t b16 = (b + 15) & ~uintptr_t(15), e16 = e & ~uintptr_t(15);   // inside the job's symbols
+            if (e16 > b16)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b16), "r"((uint32_t)(e16 - b16)) : "memory");
+        }
+        // ---- load and transpose: plane k holds code bit rb-1-k of every symbol;
+        //      the zeros of plane 0 in this warp's range
         {
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             uint32_t x[8];
             load32(tile, rt.in_w, 32u * w0, m, shift, x);
-            store_planes(x, h, h, sm.plane[0], w0);
+            const uint32_t f0 = store_planes(x, h, h, sm.plane[0], w0);
             load32(tile, rt.in_w, 32u * w0 + 32u, m, shift, x);
-            store_planes(x, h, h, sm.plane[0], w0 + 1);
+            const uint32_t f1 = store_planes(x, h, h, sm.plane[0], w0 + 1);
+            const uint32_t z = __reduce_add_sync(kFull, __popc(~f0) + __popc(~f1));
+            if (lane == 0) sm.wz[0][warp] = z;
         }
         __syncthreads();
 
+#pragma unroll(H == 8 ? 8 : 1)
         for (uint32_t l = 0; l < h; ++l) {
             uint32_t(*cur)[kBsWords + 2] = sm.plane[l & 1];
             uint32_t(*nxt)[kBsWords + 2] = sm.plane[(l + 1) & 1];
             const uint32_t base = 1u << l;
             // plane l in tile order is level l; zero counts of this thread's words
-            const uint32_t m0 = cur[l][w0], m1 = cur[l][w0 + 1];
-            sm.lvl[w0] = m0;
-            sm.lvl[w0 + 1] = m1;
+            const uint2 mm = *reinterpret_cast<const uint2 *>(&cur[l][w0]);
+            const uint32_t m0 = mm.x, m1 = mm.y;
             const uint32_t z0 = __popc(~m0), z1 = __popc(~m1);
             uint32_t inc = z0 + z1;
 #pragma unroll
@@ -947,23 +1160,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 if (lane >= (uint32_t)d) inc += y;
             }
             const uint32_t zl = inc - z0 - z1;             // zeros before word w0 inside the warp
-            if (lane == 31) sm.wsum[warp] = inc;
-            __syncthreads();
-            // zeros before each warp's range; total zeros Z of the tile
-            const uint32_t ws = lane < (uint32_t)kWarps ? sm.wsum[lane] : 0u;
+            // zeros before each warp's range (counted when plane l was placed); total Z
+            const uint32_t ws = lane < (uint32_t)kWarps ? sm.wz[l][lane] : 0u;
             uint32_t wex = ws;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
+            for (int d = 1; d < kWarps; d <<= 1) {
                 const uint32_t y = __shfl_up_sync(kFull, wex, d);
                 if (lane >= (uint32_t)d) wex += y;
             }
-            const uint32_t zt = __shfl_sync(kFull, wex, 31);
-            wex -= ws;                                      // lane j: zeros before warp j's words
-            const uint32_t zo = __shfl_sync(kFull, wex, warp) + zl;
-
+            const uint32_t zt = __shfl_sync(kFull, wex, kWarps - 1);
+            const uint32_t zw = __shfl_sync(kFull, wex - ws, warp);   // zeros before this warp's range
+            const uint32_t zo = zw + zl;
 
             // copy every class's bits to its interval start in level c + l (for
-            // kBoth: in the WT's levels, then in the WM's)
+            // kBoth: in the WT's levels, then in the WM's).  Consecutive tiles of the
+            // group put a class's runs one after the other, so a word shared by two
+            // tiles' runs is finished by the later tile: the earlier one leaves its
+            // bits in pend and the later one stores the whole word.  Only words shared
+            // with another group's runs are updated in place (and-not, then or), the
+            // bits of this group only (single output; kBoth updates every partial word
+            // in place).
+            const uint32_t *lvl = cur[l];
+            const bool first_tile = tix == 0, last_tile = t0 + kBsTile >= g_end;
             for (uint32_t out = 0; out < (both ? 2u : 1u); ++out) {
                 const uint32_t wt = out ? sm.wtot2[l] : sm.wtot[l];
                 const uint8_t *wc = out ? sm.wcls2[l] : sm.wcls[l];
@@ -979,40 +1197,83 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     const uint32_t blo = rel ? 0u : g0;
                     uint32_t bhi = min(c + g0 - 64u * rel, 64u);
                     const uint32_t src = sm.loc[idx] + 64u * rel + blo - g0;
-                    const uint64_t val = run_bits(sm.lvl, src, bhi - blo) << blo;
+                    const uint64_t val = run_bits(lvl, src, bhi - blo) << blo;
                     const uint64_t word = (uint64_t)(gs >> 6) + rel;
                     if ((uint64_t)gs + c == t.n) bhi = 64;   // bits past n belong to the last interval
-                    if (blo == 0 && bhi == 64) {
-                        lv[word] = val;
+                    if (both) {
+                        if (blo == 0 && bhi == 64) {
+                            lv[word] = val;
+                        } else {
+                            const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
+                            atomicAnd(reinterpret_cast<unsigned long long *>(lv + word), ~msk);
+                            atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
+                        }
+                        continue;
+                    }
+                    const uint32_t gq = sm.gst[idx];
+                    const bool tail = ((gs + c - 1u) >> 6) == (gs >> 6) + rel;
+                    uint64_t v = val;
+                    if (rel == 0 && !first_tile) v |= sm.pend[(tix - 1) & 1][idx];
+                    // this group's bits in the word start at lo (> 0 only in the group's first
+                    // word of the class, when an earlier group's run ends in it)
+                    const uint32_t lo = word == (uint64_t)(gq >> 6) ? (gq & 63u) : 0u;
+                    if (bhi < 64 && !last_tile) {
+                        sm.pend[tix & 1][idx] = v;            // the next tile finishes the word
+                    } else if (lo == 0 && bhi == 64) {
+                        lv[word] = v;
+                        if (tail) sm.pend[tix & 1][idx] = 0;
                     } else {
-                        const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
+                        const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << lo) - 1ull);
                         atomicAnd(reinterpret_cast<unsigned long long *>(lv + word), ~msk);
-                        atomicOr(reinterpret_cast<unsigned long long *>(lv + word), val);
+                        atomicOr(reinterpret_cast<unsigned long long *>(lv + word), v);
+                        if (tail) sm.pend[tix & 1][idx] = 0;
                     }
                 }
             }
 
             // stable split of every later plane by plane l
             if (l + 1 < h) {
-                uint32_t mz0[5], mo0[5], mz1[5], mo1[5];
-                compress_moves_split(m0, mz0, mo0);
-                compress_moves_split(m1, mz1, mo1);
-                const uint32_t dz = zo, d1 = zt + w0 * 32u - zo;
+                ByteSplit s0, s1;
+                byte_split(m0, s0);
+                byte_split(m1, s1);
                 const uint32_t nz = z0 + z1, no = 64u - nz;
-                const uint32_t kz0 = z0 == 32u ? ~0u : (1u << z0) - 1u;
-                const uint32_t ko0 = z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u;
-                const uint32_t kz1 = z1 == 32u ? ~0u : (1u << z1) - 1u;
-                const uint32_t ko1 = z1 == 0u ? ~0u : (1u << (32u - z1)) - 1u;
-                for (uint32_t k = l + 1; k < h; ++k) {
-                    const uint32_t x0 = cur[k][w0], x1 = cur[k][w0 + 1];
-                    const uint64_t pz = (uint64_t)compress_apply(x0, kz0, mz0) |
-                                        ((uint64_t)compress_apply(x1, kz1, mz1) << z0);
-                    const uint64_t po = (uint64_t)compress_apply(x0, ko0, mo0) |
-                                        ((uint64_t)compress_apply(x1, ko1, mo1) << (32u - z0));
-                    place_bits(nxt[k], dz, pz, nz);
-                    place_bits(nxt[k], d1, po, no);
-                    cur[k][w0] = 0;
-                    cur[k][w0 + 1] = 0;
+                const uint32_t dz = zo, d1 = zt + w0 * 32u - zo;
+                const Dest dzs = make_dest(nxt, dz, nz), dos = make_dest(nxt, d1, no);
+                // the second word's part follows the first's z0 (32 - z0) bits
+                const uint32_t o0 = 32u - z0;
+                const uint32_t mz = z0 < 32u ? 1u << z0 : 0u, mo = o0 < 32u ? 1u << o0 : 0u;
+                // the warp's zeros run starts in range zw / kRangeBits, its ones run in
+                // range (zt + 2048 warp - zw) / kRangeBits; each spans at most two ranges
+                const uint32_t rz0 = zw / kRangeBits, ro0 = (zt + (uint32_t)kRangeBits * warp - zw) / kRangeBits;
+                const uint32_t nk = H ? (uint32_t)H : h;
+#pragma unroll
+                for (uint32_t k = 1; k < (H ? (uint32_t)H : (uint32_t)kChunk); ++k) {
+                    if (k <= l || k >= nk) continue;
+                    const uint2 xx = *reinterpret_cast<const uint2 *>(&cur[k][w0]);
+                    *reinterpret_cast<uint2 *>(&cur[k][w0]) = make_uint2(0u, 0u);
+                    const uint32_t cz0 = byte_compress(xx.x, s0.rz, s0.kz, s0.jz);
+                    const uint32_t cz1 = byte_compress(xx.y, s1.rz, s1.kz, s1.jz);
+                    const uint32_t co0 = byte_compress(xx.x, s0.ro, s0.ko, s0.jo);
+                    const uint32_t co1 = byte_compress(xx.y, s1.ro, s1.ko, s1.jo);
+                    const uint32_t zlo = mad_lo(cz1, mz, cz0), zhi = z0 < 32u ? mul_hi(cz1, mz) : cz1;
+                    const uint32_t olo = mad_lo(co1, mo, co0), ohi = o0 < 32u ? mul_hi(co1, mo) : co1;
+                    place_part(dzs, k, zlo, zhi);
+                    place_part(dos, k, olo, ohi);
+                    if (k == l + 1) {                   // the next level's zeros per warp range
+                        uint32_t a0, b0, a1, b1;
+                        range_zeros(dz, nz, ((uint64_t)zhi << 32) | zlo, rz0, a0, b0);
+                        range_zeros(d1, no, ((uint64_t)ohi << 32) | olo, ro0, a1, b1);
+                        a0 = __reduce_add_sync(kFull, a0);
+                        b0 = __reduce_add_sync(kFull, b0);
+                        a1 = __reduce_add_sync(kFull, a1);
+                        b1 = __reduce_add_sync(kFull, b1);
+                        if (lane == 0) {
+                            if (a0) atomicAdd(&sm.wz[k][rz0], a0);
+                            if (b0) atomicAdd(&sm.wz[k][rz0 + 1], b0);
+                            if (a1) atomicAdd(&sm.wz[k][ro0], a1);
+                            if (b1) atomicAdd(&sm.wz[k][ro0 + 1], b1);
+                        }
+                    }
                 }
                 if (tid == 0)
                     for (uint32_t k = l + 1; k < h; ++k) cur[k][kBsWords] = cur[k][kBsWords + 1] = 0;
@@ -1141,9 +1402,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                 __syncthreads();
             }
         }
-        // leaf counts of this tile advance the job offsets for the next tile
-        for (uint32_t q = tid; q < (1u << h); q += kThreads) sm.offq[q] += sm.cnt[(1u << h) + q];
-        __syncthreads();
     }
 }
 
@@ -1353,7 +1611,8 @@ cudaError_t configure_kernels()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
     if (e != cudaSuccess) return e;
-    for (auto k : {k_build_bs<false, false>, k_build_bs<false, true>, k_build_bs<true, false>}) {
+    for (auto k : {k_build_bs<false, false, 0>, k_build_bs<false, true, 0>, k_build_bs<true, false, 0>,
+                   k_build_bs<false, false, 8>, k_build_bs<false, true, 8>, k_build_bs<true, false, 8>}) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BsSmem));
         if (e != cudaSuccess) return e;
     }
@@ -1476,12 +1735,18 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     k_blockscan<<<1, 256, 0, s>>>(a);
     k_groupexcl<<<a.blocks_ub, 256, 0, s>>>(a);
     if (prof) { profile_mark(2, false, s); profile_mark(0, true, s); }
-    if (a.kind == kBoth)
-        k_build_bs<true, false><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
-    else if (a.any_cut || a.any_order)
-        k_build_bs<false, true><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
-    else
-        k_build_bs<false, false><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    // every job of the round splits 8 levels: the instantiation with fixed loop bounds
+    const bool h8 = a.all_h8 != 0;
+    if (a.kind == kBoth) {
+        if (h8) k_build_bs<true, false, 8><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+        else k_build_bs<true, false, 0><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    } else if (a.any_cut || a.any_order) {
+        if (h8) k_build_bs<false, true, 8><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+        else k_build_bs<false, true, 0><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    } else {
+        if (h8) k_build_bs<false, false, 8><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+        else k_build_bs<false, false, 0><<<a.groups_ub, kThreads, sizeof(BsSmem), s>>>(a);
+    }
     if (a.any_small && a.kind != kBoth)           // kBoth has no small jobs
     {
         k_build_small<1, kTinyWarps><<<(a.nslots + kTinyWarps - 1) / kTinyWarps, kTinyWarps * 32,
