@@ -43,7 +43,7 @@ HBM_FALLBACK_GBS = 6800.0
 # above L2) and is scaled to the benchmark's n by symbol count; any later change to
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
-    # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (profiles/k_build_bs_bytes_n2e28_full.md)
+    # ncu --set full of k_build_bs, n = 2^28 uint8 WT build
     "fd242d804e1e1d3e690708483c2c46a32c9d6ca8a54d7e1bf563056d2b6b247a": {"dram_bytes": 344705280 + 222975488,
                                                                          "n": 1 << 28},
 }
@@ -235,6 +235,65 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def build_block(wtg, T, sigma, desc, steps, warmup, pg, world):
+    """wt_build + wm_build of a resident text per step: symbols/s, the split kernel's
+    roofline (algorithmic bytes per launch: one read of the round's input and its
+    levels' bits, averaged over the rounds) and the time per kernel family."""
+    import torch
+    n, w = T.size, T.dtype.itemsize
+    L = wtg.wt_levels(sigma)
+    W = wtg.wt_words_per_level(n)
+    host = torch.from_numpy(T.view({1: np.uint8, 2: np.int16, 4: np.int32}[w]))
+    text = host.cuda()
+    ws_t = torch.empty((wtg.wt_workspace_size(wtg.WT_TREE, w, n, sigma),), dtype=torch.uint8, device="cuda")
+    ws_m = torch.empty((wtg.wt_workspace_size(wtg.WT_MATRIX, w, n, sigma),), dtype=torch.uint8, device="cuda")
+    bv_t = torch.empty((L, W), dtype=torch.int64, device="cuda")
+    bv_m = torch.empty((L, W), dtype=torch.int64, device="cuda")
+    z = torch.empty((max(L, 1),), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        wtg.wt_build(text, sigma, bv=bv_t, ws=ws_t, stream=stream)
+        wtg.wm_build(text, sigma, bv=bv_m, zeros=z, ws=ws_m, stream=stream)
+
+    for _ in range(max(warmup, 3)):
+        step()
+    wtg.wt_sync_status(ws_t)
+    wtg.wt_sync_status(ws_m)
+    wtg.wt_profile_enable(True)
+    wtg.wt_profile_read(reset=True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = wtg.wt_profile_read(reset=True)
+    wtg.wt_profile_enable(False)
+    ms = max_over_ranks(pg, e0.elapsed_time(e1) / steps)
+    peak, peak_kind = peaks()
+    rounds = (L + 7) // 8
+    algo_bytes = n * w + n * L / 8.0
+    b_ms, b_launches = prof["build"]
+    per_launch_s = b_ms / (2 * steps * rounds) / 1e3
+    achieved = algo_bytes / rounds / per_launch_s / 1e9
+    out = {"value": world * 2 * n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "config": {"workload": desc, "n": n, "sigma": sigma, "levels": L, "rounds": rounds,
+                      "builds_per_step": 2},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "k_build_bs (one launch per round; bytes averaged over the rounds)",
+                        "peak_kind": peak_kind},
+           "step_roofline_frac": (2 * algo_bytes / (ms / 1e3) / 1e9) / peak,
+           "breakdown": {f: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
+                         for f, v in prof.items()},
+           "gpu_launches_per_step": sum(v[1] for v in prof.values()) / steps + 1}
+    return out, (bv_t, bv_m, z)
 
 
 def run_ours(args):
@@ -438,6 +497,17 @@ def run_ours(args):
                       "bytes_per_input_byte": (n * w + out_b + max(ws_t.numel(), ws_m.numel())) / (n * w)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(T, sigma, args.oracle_sample_log2)
+    if args.workload == "bytes" and args.n_log2 is None and not args.no_extra:
+        # the other configurations of the benchmark, measured in the same run:
+        # the large-alphabet text and the batched build against per-text launches
+        del text, ws_t, ws_m, bv_t, bv_m, z
+        torch.cuda.empty_cache()
+        TL, sl, dl = load_workload("large_alphabet")
+        blk, _ = build_block(wtg, TL, sl, dl, max(2, args.steps // 4), args.warmup, pg, world)
+        line["large_alphabet"] = blk
+        del TL, blk
+        torch.cuda.empty_cache()
+        line["batched"] = batched_block(args, pg, world)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -456,13 +526,15 @@ def batched_roofline(texts, sigmas, ms):
             "traffic": None, "kernel": "whole step (all kernels of both graph replays)", "peak_kind": peak_kind}
 
 
-def run_batched(args):
+def batched_block(args, pg, world, steps=None):
+    """4096 texts: one CUDA-graph replay per kind per step (block size chosen by the
+    autotuner) against one wt_build / wm_build call per text, every batched output
+    checked equal to the per-text build's."""
     import torch
     import paper_1702_07578_gb300 as wtg
     import synth
 
-    rank, local, world, pg = dist()
-    torch.cuda.set_device(local)
+    steps = steps or max(2, args.steps // 4)
     count = args.batch_count
     specs = synth.batch_specs(count)
     texts_h = synth.batch_texts(specs)
@@ -477,16 +549,17 @@ def run_batched(args):
         zz = [torch.empty((max(wtg.wt_levels(sg), 1),), dtype=torch.int64, device="cuda") for sg in sigmas]
         return bv, zz
 
-    res = {}
     tune = os.path.join(tempfile.gettempdir(), f"wt_tune_{os.getpid()}.json")
     os.environ.setdefault("WT_TUNE_CACHE", tune)
-    plans = {}
+    plans, outs = {}, {}
     for kind in (wtg.WT_TREE, wtg.WT_MATRIX):
         bv, zz = outputs()
         best = wtg.wt_autotune_batched(kind, texts, sigmas, bv, zz if kind else None, stream=stream)
         plans[kind] = (wtg.WtBatchPlan(kind, texts, sigmas, bv, zz if kind else None, stream=stream), best)
+        outs[kind] = (bv, zz)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    wtg.wt_profile_enable(False)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             for kind in plans:
@@ -494,24 +567,25 @@ def run_batched(args):
         stream.synchronize()
         barrier(pg)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             for kind in plans:
                 plans[kind][0].launch()
         e1.record(stream)
         stream.synchronize()
-    ms = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
+    ms = max_over_ranks(pg, e0.elapsed_time(e1) / steps)
     value = world * 2 * total / (ms / 1e3)
 
     # the same texts, one plain build per text (per-text workspace, resident inputs)
     ws = [torch.empty((max(wtg.wt_workspace_size(wtg.WT_TREE, 2, t.numel(), sg),
                            wtg.wt_workspace_size(wtg.WT_MATRIX, 2, t.numel(), sg)),),
                       dtype=torch.uint8, device="cuda") for t, sg in zip(texts, sigmas)]
-    bvp, zzp = outputs()
+    bvt, _ = outputs()
+    bvm, zzm = outputs()
 
     def plain_step():
         for i, (t, sg) in enumerate(zip(texts, sigmas)):
-            wtg.wt_build(t, sg, bv=bvp[i], ws=ws[i], stream=stream)
-            wtg.wm_build(t, sg, bv=bvp[i], zeros=zzp[i], ws=ws[i], stream=stream)
+            wtg.wt_build(t, sg, bv=bvt[i], ws=ws[i], stream=stream)
+            wtg.wm_build(t, sg, bv=bvm[i], zeros=zzm[i], ws=ws[i], stream=stream)
 
     with torch.cuda.stream(stream):
         plain_step()
@@ -522,25 +596,40 @@ def run_batched(args):
         e1.record(stream)
         stream.synchronize()
         plain_wall = time.perf_counter() - t0
-    plain_ms = max(e0.elapsed_time(e1), plain_wall * 1e3)
+    plain_ev = e0.elapsed_time(e1)
+    plain_ms = max(plain_ev, plain_wall * 1e3)
+    # identical output: every text's batched levels (and Z) equal its own build's
+    same = all(torch.equal(a, b) for a, b in zip(outs[wtg.WT_TREE][0], bvt))
+    same = same and all(torch.equal(a, b) for a, b in zip(outs[wtg.WT_MATRIX][0], bvm))
+    same = same and all(torch.equal(a[:max(wtg.wt_levels(sg), 1)], b[:max(wtg.wt_levels(sg), 1)])
+                        for a, b, sg in zip(outs[wtg.WT_MATRIX][1], zzm, sigmas) if wtg.wt_levels(sg))
+    assert same, "batched output differs from the per-text builds"
     plain_value = world * 2 * total / (plain_ms / 1e3)
+    return {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "config": {"workload": f"{count} texts, length floor(2^(10+10u)), sigma in {{2^4,2^8,2^12,2^16}}, "
+                                   f"uint16, Zipf(0.8) over per-text permutations",
+                       "symbols": total, "builds_per_step": 2 * count,
+                       "symbols_per_block": {"wt": plans[0][1], "wm": plans[1][1]},
+                       "launch": "one CUDA graph replay per kind per step"},
+            "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
+                      "device_ms_per_step": plain_ev, "host_wall_ms_per_step": plain_wall * 1e3,
+                      "launch": f"{2 * count} wt_build/wm_build calls per step"},
+            "identical_output": same,
+            "speedup_vs_plain": value / plain_value,
+            "roofline": batched_roofline(texts_h, sigmas, ms)}
+
+
+def run_batched(args):
+    import torch
+    rank, local, world, pg = dist()
+    torch.cuda.set_device(local)
+    blk = batched_block(args, pg, world, steps=args.steps)
     if rank != 0:
         return 0
-    line = {
-        "metric": "input symbols/s, batched WT+WM construction (4096 texts) vs per-text launches",
-        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u16", "data": "synthetic",
-        "config": {"workload": f"{count} texts, length floor(2^(10+10u)), sigma in {{2^4,2^8,2^12,2^16}}, "
-                               f"uint16, Zipf(0.8) over per-text permutations",
-                   "symbols": total, "builds_per_step": 2 * count,
-                   "symbols_per_block": {"wt": plans[0][1], "wm": plans[1][1]},
-                   "launch": "one CUDA graph replay per kind per step"},
-        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
-                  "launch": f"{2 * count} wt_build/wm_build calls per step"},
-        "speedup_vs_plain": value / plain_value,
-        "roofline": batched_roofline(texts_h, sigmas, ms),
-    }
+    line = {"metric": "input symbols/s, batched WT+WM construction (4096 texts) vs per-text launches",
+            "n_gpus": world, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic"}
+    line.update(blk)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -897,6 +986,8 @@ def main(argv=None):
                     help="text length 2^k (smaller cases for profiler captures)")
     ap.add_argument("--oracle-sample-log2", type=int, default=26)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: leave out the large-alphabet and batched blocks")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per k_build launch from an ncu capture (reported as is)")
     args = ap.parse_args(argv)

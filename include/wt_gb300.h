@@ -184,14 +184,18 @@ wt_status wt_build_host(const void *h_text, wt_symtype type, uint64_t n, uint64_
  * loads the library holds until the process exits.  The caller still passes the text and the output buffer.  The call
  * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *
- * Limit: texts whose workspace (wt_workspace_size(WT_TREE, ...)) exceeds the
- * capacity are rejected with WT_ERR_OUT_OF_MEMORY before anything is
- * launched.  With sigma <= 256 that allows about 16 million symbols; larger
- * alphabets also need a re-sorted copy of the text (2 or 4 bytes per symbol)
- * and allow far fewer.
+ * Limit: a text is accepted when wt_workspace_size(WT_TREE, type, n, sigma)
+ * is at most 1,048,576 bytes (the exact test); larger ones are rejected with
+ * WT_ERR_OUT_OF_MEMORY before anything is launched.  That is n <= 11,010,048
+ * symbols for sigma <= 256, n <= 948,736 for sigma = 257 and n <= 882,688 for
+ * sigma = 4096 (uint16 storage; alphabets above 256 also need a re-sorted copy
+ * of the text), and no text at all for sigma = 65536 or more (the per-subtree
+ * tables of the later rounds alone exceed the array).
  *
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current); make that first call before any stream capture.  The call
+ * reads no host memory on the stream: the text's descriptor reaches the array
+ * as a kernel argument.  All calls
  * share the one array and every call re-initialises what it reads from it, so
  * calls are correct one after the other; two calls that overlap on the GPU
  * (different streams, or different host threads) race on the array and give

@@ -262,10 +262,13 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
         a.groups_ub = p.groups_ub[r];
         a.blocks_ub = p.blocks_ub[r];
         a.all_h8 = 1;
+        uint32_t in_w = 1;                          // widest symbol read by the round
         for (uint32_t i = 0; i < p.count; ++i) {
             const TextInfo &ti = p.texts[i];
             if (ti.nslots[r] == 0) continue;
             if (round_levels(ti.L, r) != (uint32_t)kChunk) a.all_h8 = 0;
+            const uint32_t w = r == 0 ? ti.in_w : width_for_bits(ti.L - round_first_level(ti.L, r));
+            if (w > in_w) in_w = w;
             const bool last = r + 1 == round_count(ti.L);
             if (!last) a.any_cut = 1; else a.any_plain = 1;
             if (ti.perm != nullptr) a.any_order = 1;
@@ -275,7 +278,7 @@ wt_status launch(wt_kind kind, const Plan &p, void *d_ws, cudaStream_t s)
                 ((kind == WT_TREE && r > 0) || (ti.n > 0 && ti.n <= kSmallJob)))
                 a.any_small = 1;
         }
-        if (launch_round(a, p.width[r], s) != cudaSuccess) return WT_ERR_CUDA;
+        if (launch_round(a, in_w, s) != cudaSuccess) return WT_ERR_CUDA;
     }
     return WT_OK;
 }
@@ -707,6 +710,13 @@ __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
 std::mutex g_static_mu;
 void *g_static_ptr[64] = {};
 
+// The text's descriptor written into the scratch from a kernel argument, so that
+// the call reads no host memory on the stream.
+__global__ void k_put_text(TextInfo *dst, TextInfo v)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+
 // Device address of g_static_scratch on the current device (looked up once per device).
 wt_status static_scratch(void **out)
 {
@@ -737,7 +747,13 @@ extern "C" wt_status wt_build_static_ws(const void *d_text, wt_symtype type, uin
     void *ws = nullptr;
     st = static_scratch(&ws);
     if (st != WT_OK) return st;
-    return run_plan(WT_TREE, p, ws, kStaticScratchBytes, static_cast<cudaStream_t>(stream));
+    st = prepare(p, ws, kStaticScratchBytes);
+    if (st != WT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TextInfo *dtexts = reinterpret_cast<TextInfo *>(static_cast<uint8_t *>(ws) + p.off_texts);
+    k_put_text<<<1, 32, 0, s>>>(dtexts, p.texts[0]);
+    if (cudaGetLastError() != cudaSuccess) return WT_ERR_CUDA;
+    return launch(WT_TREE, p, ws, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -140,8 +140,9 @@ wt_status build_with_counts(wt_kind kind, const void *d_text, wt_symtype type, u
 cudaError_t launch_identity_order(const void *text, uint32_t w, uint64_t n, uint32_t *perm, void *sorted,
                                   cudaStream_t s);
 
-// Launches one round on the stream.  Returns a CUDA error code.
-cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s);
+// Launches one round on the stream; in_w: the widest symbol (bytes) the round reads.
+// Returns a CUDA error code.
+cudaError_t launch_round(const RoundArgs &a, uint32_t in_w, cudaStream_t s);
 
 // Device pass that marks every text's Z as zero (WM) before round 0.
 cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s);

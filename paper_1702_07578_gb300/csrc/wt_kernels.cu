@@ -367,10 +367,20 @@ __global__ void __launch_bounds__(1024) k_scan_chunks(RoundArgs a, uint32_t pass
 // workload: per-warp copies cost more in their per-tile reduction (every tile
 // row sums all copies) and in shared memory per block than they save in
 // same-class atomics, and small blocks (8 per SM) keep more loads in flight.
+// Rounds whose symbols are all bytes use per-lane columns instead (LC): class q
+// of lane i is word 32q + i, so the 32 atomics of a warp instruction always fall
+// in 32 different banks and never on one address, whatever the skew; a tile's
+// row sums the 32 columns of each class with a rotated read.  That takes 32 KB
+// per block, which the passes over 2- and 4-byte symbols (fewer symbols per
+// byte read) do not repay.  Warp-aggregated counting (one atomic per distinct
+// class of a warp instruction, found with a warp match) was measured 15 times
+// slower: the match costs far more than the atomics it saves.
 constexpr int kHistThreads = 256;
 constexpr size_t kHistSmem = sizeof(uint32_t) * kCols;
+constexpr size_t kHistSmemLC = sizeof(uint32_t) * kCols * 32;
 
-__global__ void __launch_bounds__(kHistThreads, 8) k_hist(RoundArgs a)
+template <bool LC>
+__global__ void __launch_bounds__(kHistThreads, LC ? 6 : 8) k_hist(RoundArgs a)
 {
     extern __shared__ __align__(16) uint32_t wh[];
     const uint32_t g = blockIdx.x;
@@ -385,13 +395,15 @@ __global__ void __launch_bounds__(kHistThreads, 8) k_hist(RoundArgs a)
     const bool check = a.round == 0 && t.sigma < (1ull << t.L);
     const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
     uint32_t *mine = wh;
+    const uint32_t col = LC ? threadIdx.x & 31u : 0u;   // this lane's column
+    constexpr uint32_t stride = LC ? 32u : 1u;          // words per class
     bool bad = false;
     const uint8_t *base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
     const uint32_t top = a.round == 0 && t.L < 8 ? (0xffu << t.L) & 0xffu : 0u;
     const uint32_t top4 = top * 0x01010101u;
     const uint32_t tile_first = jb.tile0 + (uint32_t)(g0 / kTileSyms);
     uint32_t gsum = 0;                                   // running group count of column threadIdx.x
-    for (uint32_t i = threadIdx.x; i < (uint32_t)kCols; i += kHistThreads) wh[i] = 0;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kCols * stride; i += kHistThreads) wh[i] = 0;
     __syncthreads();
     // one tile (kTileSyms symbols) at a time; a tile's row is the difference of
     // the running counts after and before it
@@ -420,26 +432,32 @@ __global__ void __launch_bounds__(kHistThreads, 8) k_hist(RoundArgs a)
                         bad |= (x & top4) != 0u;
                         if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) atomicAdd(&mine[((x >> (8 * b + shift)) & mask)], 1u);
+                        for (int b = 0; b < 4; ++b) atomicAdd(&mine[stride * ((x >> (8 * b + shift)) & mask) + col], 1u);
                     }
                 }
             }
             for (uint64_t i = i0 + nchunks * 16 + threadIdx.x; i < i1; i += kHistThreads) {
                 const uint32_t x = base[i];
                 bad |= (check && x >= sig) || (x & top) != 0u;
-                atomicAdd(&mine[(x >> shift) & mask], 1u);
+                atomicAdd(&mine[stride * ((x >> shift) & mask) + col], 1u);
             }
         } else {
             for_range(base, rt.in_w, i0, i1, [&](uint32_t, uint32_t v) {
                 bad |= check && v >= sig;
                 bad |= a.round == 0 && t.L < 32 && (v >> t.L) != 0;
-                atomicAdd(&mine[(v >> shift) & mask], 1u);
+                atomicAdd(&mine[stride * ((v >> shift) & mask) + col], 1u);
             });
         }
         __syncthreads();
         static_assert(kHistThreads == kCols, "one column per thread");
         {
-            const uint32_t s = wh[threadIdx.x];
+            uint32_t s = 0;
+            if (LC) {
+#pragma unroll 8
+                for (uint32_t j = 0; j < 32u; ++j) s += wh[32u * threadIdx.x + ((j + threadIdx.x) & 31u)];
+            } else {
+                s = wh[threadIdx.x];
+            }
             a.thist[((size_t)tile_first + tix) * kCols + threadIdx.x] = s - gsum;
             gsum = s;
         }
@@ -1609,7 +1627,9 @@ cudaError_t configure_kernels()
     e = cudaFuncSetAttribute(k_build_small<kSmallWords, kSmallWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(SmallSmem<kSmallWords>) * kSmallWarps));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
+    e = cudaFuncSetAttribute(k_hist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmemLC);
     if (e != cudaSuccess) return e;
     for (auto k : {k_build_bs<false, false, 0>, k_build_bs<false, true, 0>, k_build_bs<true, false, 0>,
                    k_build_bs<false, false, 8>, k_build_bs<false, true, 8>, k_build_bs<true, false, 8>}) {
@@ -1708,7 +1728,7 @@ cudaError_t launch_zero_z(const TextInfo *texts, uint32_t ntexts, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s)
+cudaError_t launch_round(const RoundArgs &a, uint32_t in_w, cudaStream_t s)
 {
     if (a.nslots == 0) return cudaSuccess;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1729,7 +1749,8 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t smem_width, cudaStream_t s
     if (prof) profile_mark(3, false, s);
     if (a.groups_ub == 0) return cudaGetLastError();
     if (prof) profile_mark(1, true, s);
-    k_hist<<<a.groups_ub, kHistThreads, kHistSmem, s>>>(a);
+    if (in_w == 1) k_hist<true><<<a.groups_ub, kHistThreads, kHistSmemLC, s>>>(a);   // byte rounds
+    else k_hist<false><<<a.groups_ub, kHistThreads, kHistSmem, s>>>(a);
     if (prof) { profile_mark(1, false, s); profile_mark(2, true, s); }
     k_blocksum<<<a.blocks_ub, 256, 0, s>>>(a);
     k_blockscan<<<1, 256, 0, s>>>(a);
