@@ -1066,12 +1066,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                         const uint64_t v = sm.pend[(tix - 1) & 1][idx];
                         sm.pend[tix & 1][idx] = v;
                         // the group's last tile has no run of this class: the bits its
-                        // earlier tiles left in the word gs / 64 are written now
-                        if (t0 + kBsTile >= g_end && (gs & 63u) != 0) {
+                        // earlier tiles left in the word gs / 64 are written now (none
+                        // are left when the class's run ended on a word boundary, or
+                        // at n, where the word was finished with the bits past n)
+                        if (t0 + kBsTile >= g_end && (gs & 63u) != 0 && (uint64_t)gs != t.n) {
                             const uint32_t gq = sm.gst[idx];
                             const uint32_t lo = (gs >> 6) == (gq >> 6) ? (gq & 63u) : 0u;
-                            const uint64_t upto = (uint64_t)gs == t.n ? ~0ull : ((1ull << (gs & 63u)) - 1ull);
-                            const uint64_t msk = upto & ~((1ull << lo) - 1ull);   // bits past n belong to the last interval
+                            const uint64_t msk = ((1ull << (gs & 63u)) - 1ull) & ~((1ull << lo) - 1ull);
                             if (msk != 0) {
                                 unsigned long long *w = reinterpret_cast<unsigned long long *>(
                                     t.bv + (uint64_t)(rt.c + l) * t.W + (gs >> 6));

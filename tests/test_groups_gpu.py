@@ -20,6 +20,14 @@ def _text(n, sigma, dist, seed, dtype):
         return synth.zipf_text(n, sigma, 1.0, seed, dtype)
     if dist == "uniform":
         return synth.uniform_text(n, sigma, seed, dtype)
+    if dist == "lowtail":
+        # the last tile holds only the lower half of the alphabet: at every level
+        # below the first, the last interval's class (all ones) is empty there and
+        # its run ends at n inside an earlier tile of the last group
+        T = synth.uniform_text(n, sigma, seed, dtype)
+        k = (n - 1) // TILE * TILE
+        T[k:] = synth.uniform_text(n - k, max(1, sigma // 2), seed + 1, dtype)
+        return T
     # half uniform, then a long run of one symbol, then sparse rare symbols: most
     # classes are empty in many consecutive tiles
     T = synth.uniform_text(n, sigma, seed, dtype)
@@ -40,6 +48,9 @@ CASES = [
     (200_000, 2, "uniform", np.uint8),
     (400_003, 4096, "zipf", np.uint16),
     (262_144, 97, "zipf", np.uint8),
+    (3 * 32768 + 1000, 256, "lowtail", np.uint8),
+    (6 * 32768 + 77, 256, "lowtail", np.uint16),
+    (5 * 32768 + 4001, 4096, "lowtail", np.uint16),
 ]
 
 
