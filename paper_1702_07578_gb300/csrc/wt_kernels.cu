@@ -595,6 +595,7 @@ constexpr int kBsTile = kBsWords * 32;        // 32768 symbols per tile
 constexpr int kRangeBits = 64 * 32;           // positions of one warp's words (2048)
 static_assert(kBsTile == kTileSyms, "tile histograms are written per kTileSyms symbols");
 static_assert(kRangeBits * kWarps == kBsTile, "each warp owns one range of the tile");
+static_assert(kWarps >= 2 * kChunk, "two warps per level build the tile tables");
 
 struct BsSmem {
     uint32_t plane[2][kChunk][kBsWords + 2];  // current / next planes (+ overflow words)
@@ -1120,9 +1121,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                           [&](uint32_t i) { return rev_bits(i, l); },
                           [&](uint32_t q, uint32_t v) { sm.loc[base + q] = v; });
         }
-        if (warp < h || (both && warp < 2 * h)) {  // destination words: warp h + l does the WM's (kBoth)
-            const bool second = warp >= h;
-            const uint32_t l = second ? warp - h : warp, base = 1u << l;
+        // destination words: warp 8 + l for level l, so that the table work of the
+        // tile start is spread over all warps (kBoth: warp l the WT's, warp h + l the WM's)
+        if (both ? warp < 2 * h : (warp >= (uint32_t)kChunk && warp - (uint32_t)kChunk < h)) {
+            const bool second = both && warp >= h;
+            const uint32_t l = both ? (second ? warp - h : warp) : warp - (uint32_t)kChunk, base = 1u << l;
             const uint32_t *glo = second ? sm.glo2 : sm.glo;
             uint32_t *wpre = second ? sm.wpre2 : sm.wpre;
             const uint32_t wt = warp_scan_t<!CUT>(
@@ -1310,8 +1313,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                         }
                     }
                 }
-                if (tid == 0)
-                    for (uint32_t k = l + 1; k < h; ++k) cur[k][kBsWords] = cur[k][kBsWords + 1] = 0;
             }
             __syncthreads();
         }
