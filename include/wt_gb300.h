@@ -404,6 +404,47 @@ typedef struct {
 void wt_profile_enable(int on);
 wt_status wt_profile_read(wt_profile *out, int reset);
 
+/* ---- bounds checks (a debug build of the library) -------------------------
+ * The paper has no counterpart: these calls check the construction kernels'
+ * own indexing, in place of a memory checker.  When the library is compiled
+ * with -DWT_DEBUG_BOUNDS, the construction kernels (histogram pass, split
+ * kernels, small-job kernel) compare every index of a global or shared access
+ * whose bound is not evident from the loop around it with the size of the
+ * buffer it addresses: symbols read inside the text (or the round's buffer),
+ * bit-vector words inside L * W, histogram and job rows inside the round's
+ * tables, shared-memory indexes inside their arrays, re-sorted symbols written
+ * below n.  A failed check skips that access (the output is then wrong) and
+ * counts; the first failure's site, index and bound are kept.  The default
+ * build compiles no checks and runs the same code as before.
+ *
+ * wt_debug_bounds_read: the report of the device that is current, after a
+ * cudaDeviceSynchronize; reset != 0 clears it afterwards.  A library built
+ * without the checks returns enabled = 0 and all zeros, touching no device.
+ * wt_debug_bounds_selftest: on `stream`, evaluates one check that fails (site
+ * WT_BOUNDS_SELFTEST, index 1, bound 1) and one that holds, with no memory
+ * access behind either, so that a test can see that failures are recorded.
+ * WT_ERR_INVALID_ARG in a build without the checks. */
+typedef enum {
+    WT_BOUNDS_SELFTEST = 0,   /* wt_debug_bounds_selftest                     */
+    WT_BOUNDS_TEXT = 1,       /* a symbol read past the text / round buffer   */
+    WT_BOUNDS_LEVEL = 2,      /* a bit-vector word outside L * W              */
+    WT_BOUNDS_TABLE = 3,      /* a job, group or tile row outside the round's */
+    WT_BOUNDS_SHARED = 4,     /* a shared-memory index outside its array      */
+    WT_BOUNDS_NEXT = 5        /* a re-sorted symbol or position at >= n       */
+} wt_bounds_site;
+
+typedef struct {
+    uint32_t enabled;         /* 1: this library was built with the checks    */
+    uint32_t failures;        /* failed checks since the last reset           */
+    uint32_t site;            /* first failure: a wt_bounds_site              */
+    uint32_t pad;
+    uint64_t index;           /* first failure: the index ...                 */
+    uint64_t bound;           /* ... and the bound it had to stay below       */
+} wt_bounds_report;
+
+wt_status wt_debug_bounds_read(wt_bounds_report *out, int reset);
+wt_status wt_debug_bounds_selftest(void *stream);
+
 #ifdef __cplusplus
 }
 #endif

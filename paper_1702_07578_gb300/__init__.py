@@ -322,6 +322,23 @@ def wt_profile_read(reset: bool = False):
     return {f: (p.ms[i], int(p.launches[i])) for i, f in enumerate(PROFILE_FAMILIES)}
 
 
+BOUNDS_SITES = {0: "selftest", 1: "text", 2: "level", 3: "table", 4: "shared", 5: "next"}
+
+
+def wt_debug_bounds_read(reset: bool = False):
+    """Report of the kernels' bounds checks (the WT_DEBUG_BOUNDS build): enabled,
+    failures and the first failure's site, index and bound."""
+    r = _native.WtBoundsReport()
+    _check(lib().wt_debug_bounds_read(ctypes.byref(r), 1 if reset else 0), "wt_debug_bounds_read")
+    return {"enabled": bool(r.enabled), "failures": int(r.failures),
+            "site": BOUNDS_SITES.get(int(r.site), int(r.site)), "index": int(r.index), "bound": int(r.bound)}
+
+
+def wt_debug_bounds_selftest(stream=None):
+    """One failing and one holding check on the device, with no access behind them."""
+    _check(lib().wt_debug_bounds_selftest(_stream(stream)), "wt_debug_bounds_selftest")
+
+
 class WtServer:
     """Serving loop (wt_server_*): submit host texts, wait, read or keep results on the device."""
 

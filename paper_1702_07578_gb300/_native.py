@@ -4,6 +4,11 @@
 and links them into ``_build/libwt_gb300.so``.  ``lib()`` loads it with ctypes
 and declares the C ABI of ``include/wt_gb300.h``.  There is no fallback: if the
 library is missing or fails to load, every call raises.
+
+With ``WT_DEBUG_BOUNDS=1`` in the environment (or ``build(debug_bounds=True)``)
+the same sources are compiled with ``-DWT_DEBUG_BOUNDS`` into
+``_build_dbg/libwt_gb300_dbg.so``, the build whose construction kernels check
+their indexes (``wt_debug_bounds_read``), and ``lib()`` loads that one.
 """
 from __future__ import annotations
 
@@ -20,6 +25,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT, "libwt_gb300.so")
+OUT_DBG = os.path.join(HERE, "_build_dbg")
+LIB_PATH_DBG = os.path.join(OUT_DBG, "libwt_gb300_dbg.so")
+DEBUG_ENV = "WT_DEBUG_BOUNDS"
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -43,27 +51,36 @@ def _deps():
     return files
 
 
-def _stale():
-    if not os.path.exists(LIB_PATH):
+def _debug_wanted(debug_bounds):
+    return os.environ.get(DEBUG_ENV) == "1" if debug_bounds is None else bool(debug_bounds)
+
+
+def _stale(lib_path):
+    if not os.path.exists(lib_path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib_path)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library for sm_103a (no-op when up to date)."""
+def build(force: bool = False, verbose: bool = False, debug_bounds=None) -> str:
+    """Compile the library for sm_103a (no-op when up to date).  debug_bounds:
+    the build with the kernels' bounds checks (None: the environment decides)."""
+    debug = _debug_wanted(debug_bounds)
+    out_dir, lib_path = (OUT_DBG, LIB_PATH_DBG) if debug else (OUT, LIB_PATH)
     with _lock:
-        if not force and not _stale():
-            return LIB_PATH
-        os.makedirs(OUT, exist_ok=True)
+        if not force and not _stale(lib_path):
+            return lib_path
+        os.makedirs(out_dir, exist_ok=True)
         nvcc = _nvcc()
         common = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                   "--expt-relaxed-constexpr", "-I", INCLUDE]
+        if debug:
+            common += ["-DWT_DEBUG_BOUNDS"]
         if verbose:
             common += ["-Xptxas", "-v"]
 
         def compile_one(src):
-            obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+            obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
             r = subprocess.run([nvcc, *common, "-c", src, "-o", obj],
                                capture_output=True, text=True)
             if r.returncode != 0:
@@ -76,13 +93,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             for _, err in results:
                 print(err)
-        tmp = LIB_PATH + f".{os.getpid()}.tmp"
+        tmp = lib_path + f".{os.getpid()}.tmp"
         r = subprocess.run([nvcc, ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                             "-lpthread"], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB_PATH)
-        return LIB_PATH
+        os.replace(tmp, lib_path)
+        return lib_path
 
 
 class WtTextDesc(ctypes.Structure):
@@ -116,6 +133,11 @@ class WtServerStats(ctypes.Structure):
 
 class WtProfile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_uint64 * 4)]
+
+
+class WtBoundsReport(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_uint32), ("failures", ctypes.c_uint32), ("site", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("index", ctypes.c_uint64), ("bound", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes); must cover every function of include/wt_gb300.h
@@ -187,6 +209,8 @@ SIGNATURES = {
                             _C.c_void_p, _C.c_void_p]),
     "wt_profile_enable": (None, [_C.c_int]),
     "wt_profile_read": (_C.c_int, [_C.POINTER(WtProfile), _C.c_int]),
+    "wt_debug_bounds_read": (_C.c_int, [_C.POINTER(WtBoundsReport), _C.c_int]),
+    "wt_debug_bounds_selftest": (_C.c_int, [_C.c_void_p]),
 }
 
 

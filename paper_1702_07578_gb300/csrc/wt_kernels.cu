@@ -26,6 +26,28 @@
 
 namespace wtg {
 
+// ---------------------------------------------------------------------------
+// Bounds checks, compiled in with -DWT_DEBUG_BOUNDS (the default build has
+// none: WT_IN is the constant true).  WT_IN(site, i, b) holds when i < b; a
+// failure counts, keeps the first site / index / bound, and the caller skips
+// the access it guards.
+#ifdef WT_DEBUG_BOUNDS
+__device__ wt_bounds_report g_bounds;
+
+__device__ __noinline__ bool bounds_fail(uint32_t site, uint64_t i, uint64_t b)
+{
+    if (atomicAdd(&g_bounds.failures, 1u) == 0u) {
+        g_bounds.site = site;
+        g_bounds.index = i;
+        g_bounds.bound = b;
+    }
+    return false;
+}
+#define WT_IN(site, i, b) ((uint64_t)(i) < (uint64_t)(b) || bounds_fail((site), (uint64_t)(i), (uint64_t)(b)))
+#else
+#define WT_IN(site, i, b) true
+#endif
+
 namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
@@ -386,11 +408,15 @@ __global__ void __launch_bounds__(kHistThreads, LC ? 6 : 8) k_hist(RoundArgs a)
     const uint32_t g = blockIdx.x;
     if (g >= a.ctl->total_groups[a.round]) return;
     const uint32_t slot = find_slot(a.jobs, a.nslots, g);
+    if (!WT_IN(WT_BOUNDS_TABLE, slot, a.nslots)) return;
     const Job jb = a.jobs[slot];
+    if (!WT_IN(WT_BOUNDS_TABLE, jb.text, a.ntexts)) return;
     const TextInfo &t = a.texts[jb.text];
     const RoundText rt = round_text(t, a.round);
     const uint64_t g0 = (uint64_t)(g - jb.g0) * a.gelems;
     const uint64_t g1 = min((uint64_t)jb.n, g0 + a.gelems);
+    if (!WT_IN(WT_BOUNDS_TEXT, (uint64_t)jb.off + g1, t.n + 1)) return;
+    [[maybe_unused]] const uint32_t job_rows = jb.tile0 + (uint32_t)(((uint64_t)jb.n + kTileSyms - 1) / kTileSyms);
     const uint32_t shift = rt.rb - rt.h, mask = (1u << rt.h) - 1u;
     const bool check = a.round == 0 && t.sigma < (1ull << t.L);
     const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
@@ -458,7 +484,8 @@ __global__ void __launch_bounds__(kHistThreads, LC ? 6 : 8) k_hist(RoundArgs a)
             } else {
                 s = wh[threadIdx.x];
             }
-            a.thist[((size_t)tile_first + tix) * kCols + threadIdx.x] = s - gsum;
+            if (WT_IN(WT_BOUNDS_TABLE, tile_first + tix, job_rows))
+                a.thist[((size_t)tile_first + tix) * kCols + threadIdx.x] = s - gsum;
             gsum = s;
         }
         __syncthreads();
@@ -597,6 +624,10 @@ static_assert(kBsTile == kTileSyms, "tile histograms are written per kTileSyms s
 static_assert(kRangeBits * kWarps == kBsTile, "each warp owns one range of the tile");
 static_assert(kWarps >= 2 * kChunk, "two warps per level build the tile tables");
 
+// Destination words of one level of a tile: at most kBsTile / 64 whole words
+// plus, per class, the partial words at both ends of its run.
+constexpr uint32_t kWcap = kBsWords / 2 + 2 * kCols;
+
 struct BsSmem {
     uint32_t plane[2][kChunk][kBsWords + 2];  // current / next planes (+ overflow words)
     uint64_t pend[2][kCols];                  // per level and class: bits of the group's earlier tiles in
@@ -606,9 +637,9 @@ struct BsSmem {
     uint32_t thc[kCols];                      // class counts of the tile (histogram pass)
     union {
         uint16_t cntw[kWarps][kCols];         // cut: class counts / offsets per warp chunk
-        uint8_t wcls2[kChunk][kBsWords / 2 + 2 * kCols];  // kBoth: wcls of the WM
+        uint8_t wcls2[kChunk][kWcap];         // kBoth: wcls of the WM
     };
-    uint8_t wcls[kChunk][kBsWords / 2 + 2 * kCols];   // destination word -> class, per level
+    uint8_t wcls[kChunk][kWcap];              // destination word -> class, per level
     uint32_t tP[kCols + 1];
     uint32_t offq[kCols];                     // class counts of the job before this tile
     uint32_t jP[kCols + 1];
@@ -847,6 +878,7 @@ __device__ __forceinline__ Dest make_dest(uint32_t (*buf)[kBsWords + 2], uint32_
     r.len = len;
     r.w1 = s + len > 32u;
     r.w2 = s + len > 64u;
+    if (len != 0 && !WT_IN(WT_BOUNDS_SHARED, (d >> 5) + (r.w2 ? 2u : r.w1 ? 1u : 0u), kBsWords + 2)) r.len = 0;
     return r;
 }
 
@@ -993,10 +1025,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     if (g >= a.ctl->total_groups[a.round]) return;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t slot = find_slot(a.jobs, a.nslots, g);
+    if (!WT_IN(WT_BOUNDS_TABLE, slot, a.nslots)) return;
     const Job jb = a.jobs[slot];
+    if (!WT_IN(WT_BOUNDS_TABLE, jb.text, a.ntexts)) return;
     const TextInfo &t = a.texts[jb.text];
     const RoundText rt = round_text(t, a.round);
     const uint32_t h = H ? (uint32_t)H : rt.h, rb = rt.rb;
+    if (!WT_IN(WT_BOUNDS_LEVEL, rt.c + h, t.L + 1)) return;
     const uint32_t shift = rb - h;                   // > 0 in rounds with a cut
     const uint32_t gi = g - jb.g0;
     const bool matrix = a.kind == WT_MATRIX;
@@ -1039,6 +1074,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 
     const uint64_t g_begin = (uint64_t)gi * a.gelems;
     const uint64_t g_end = min((uint64_t)jb.n, g_begin + a.gelems);
+    if (!WT_IN(WT_BOUNDS_TEXT, (uint64_t)jb.off + g_end, t.n + 1)) return;
+    [[maybe_unused]] const uint32_t job_rows = jb.tile0 + (uint32_t)(((uint64_t)jb.n + kTileSyms - 1) / kTileSyms);
     const uint8_t *in_base = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
     const uint32_t w0 = 2u * tid;                    // this thread's words: w0, w0 + 1
 
@@ -1057,7 +1094,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         if (tid < (uint32_t)kChunk) sm.plane[0][tid][kBsWords] = sm.plane[0][tid][kBsWords + 1] = 0;
         if (tid < (uint32_t)(kChunk * kWarps)) (&sm.wz[0][0])[tid] = 0;
         for (uint32_t q = tid; q < kCols; q += kThreads)
-            sm.thc[q] = a.thist[((size_t)tile_first + tix) * kCols + q];
+            sm.thc[q] = WT_IN(WT_BOUNDS_TABLE, tile_first + tix, job_rows)
+                            ? a.thist[((size_t)tile_first + tix) * kCols + q] : 0u;
         __syncthreads();
         if (warp == 0) {
             uint32_t tot = warp_scan_t<!CUT>(256, [&](uint32_t i) { return sm.thc[i]; }, [](uint32_t i) { return i; },
@@ -1095,7 +1133,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                             const uint32_t gq = sm.gst[idx];
                             const uint32_t lo = (gs >> 6) == (gq >> 6) ? (gq & 63u) : 0u;
                             const uint64_t msk = ((1ull << (gs & 63u)) - 1ull) & ~((1ull << lo) - 1ull);
-                            if (msk != 0) {
+                            if (msk != 0 && WT_IN(WT_BOUNDS_LEVEL, gs >> 6, t.W)) {
                                 red_out(t.bv + (uint64_t)(rt.c + l) * t.W + (gs >> 6), msk, v);
                             }
                         }
@@ -1128,7 +1166,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint32_t l = both ? (second ? warp - h : warp) : warp - (uint32_t)kChunk, base = 1u << l;
             const uint32_t *glo = second ? sm.glo2 : sm.glo;
             uint32_t *wpre = second ? sm.wpre2 : sm.wpre;
-            const uint32_t wt = warp_scan_t<!CUT>(
+            uint32_t wt = warp_scan_t<!CUT>(
                 base,
                 [&](uint32_t q) {
                     const uint32_t c = sm.cnt[base + q];
@@ -1137,6 +1175,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     return ((gs + c - 1) >> 6) - (gs >> 6) + 1u;
                 },
                 [](uint32_t i) { return i; }, [&](uint32_t q, uint32_t v) { wpre[base + q] = v; });
+            if (!WT_IN(WT_BOUNDS_SHARED, wt, kWcap + 1)) wt = 0;      // (the level is then not copied)
             if (lane == 0) (second ? sm.wtot2 : sm.wtot)[l] = wt;
             // word -> class map of level l: every nonempty class marks its first
             // destination word, a running maximum fills the words after it
@@ -1237,8 +1276,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     const uint32_t blo = rel ? 0u : g0;
                     uint32_t bhi = min(c + g0 - 64u * rel, 64u);
                     const uint32_t src = sm.loc[idx] + 64u * rel + blo - g0;
-                    const uint64_t val = run_bits(lvl, src, bhi - blo) << blo;
+                    const uint64_t val = WT_IN(WT_BOUNDS_SHARED, src, kBsTile) ? run_bits(lvl, src, bhi - blo) << blo : 0u;
                     const uint64_t word = (uint64_t)(gs >> 6) + rel;
+                    if (!WT_IN(WT_BOUNDS_LEVEL, word, t.W)) continue;
                     if ((uint64_t)gs + c == t.n) bhi = 64;   // bits past n belong to the last interval
                     if (both) {
                         if (blo == 0 && bhi == 64) {
@@ -1306,10 +1346,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                         a1 = __reduce_add_sync(kFull, a1);
                         b1 = __reduce_add_sync(kFull, b1);
                         if (lane == 0) {
-                            if (a0) atomicAdd(&sm.wz[k][rz0], a0);
-                            if (b0) atomicAdd(&sm.wz[k][rz0 + 1], b0);
-                            if (a1) atomicAdd(&sm.wz[k][ro0], a1);
-                            if (b1) atomicAdd(&sm.wz[k][ro0 + 1], b1);
+                            if (a0 && WT_IN(WT_BOUNDS_SHARED, rz0, kWarps)) atomicAdd(&sm.wz[k][rz0], a0);
+                            if (b0 && WT_IN(WT_BOUNDS_SHARED, rz0 + 1, kWarps)) atomicAdd(&sm.wz[k][rz0 + 1], b0);
+                            if (a1 && WT_IN(WT_BOUNDS_SHARED, ro0, kWarps)) atomicAdd(&sm.wz[k][ro0], a1);
+                            if (b1 && WT_IN(WT_BOUNDS_SHARED, ro0 + 1, kWarps)) atomicAdd(&sm.wz[k][ro0 + 1], b1);
                         }
                     }
                 }
@@ -1400,16 +1440,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     if (ok) {
                         if ((peers >> lane) == 1u) cw[q] = (uint16_t)(rank + 1u);
                         const uint64_t dst = (uint64_t)sm.glo[base_h + q] + rank;
-                        if (pstaged)
-                            stage16[sm.loc[base_h + q] + rank] = (uint16_t)e;
+                        if (pstaged) {
+                            if (WT_IN(WT_BOUNDS_SHARED, sm.loc[base_h + q] + rank, kBsTile))
+                                stage16[sm.loc[base_h + q] + rank] = (uint16_t)e;
+                        }
                         else if (pout != nullptr && dst < t.n)
                             pout[dst] = pin ? pin[pos0 + e] : (uint32_t)(pos0 + e);
                         if (rt.cut == nullptr) {
                         } else if (!staged) {
-                            store_sym(rt.cut, rt.cut_w, dst, v & low);
+                            if (WT_IN(WT_BOUNDS_NEXT, dst, t.n)) store_sym(rt.cut, rt.cut_w, dst, v & low);
                         } else {
                             const uint32_t pos = sm.loc[base_h + q] + rank;   // place in the sorted tile
-                            if (rt.cut_w == 1) stage8[pos] = (uint8_t)(v & low);
+                            if (!WT_IN(WT_BOUNDS_SHARED, pos, kBsTile)) {
+                            } else if (rt.cut_w == 1) stage8[pos] = (uint8_t)(v & low);
                             else stage16[pos] = (uint16_t)(v & low);
                         }
                     }
@@ -1422,7 +1465,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     const uint32_t c = sm.cnt[base_h + q], src = sm.loc[base_h + q];
                     const uint64_t dst = sm.glo[base_h + q];
                     for (uint32_t i = lane; i < c; i += 32)
-                        store_sym(rt.cut, rt.cut_w, dst + i, rt.cut_w == 1 ? stage8[src + i] : stage16[src + i]);
+                        if (WT_IN(WT_BOUNDS_NEXT, dst + i, t.n) && WT_IN(WT_BOUNDS_SHARED, src + i, kBsTile))
+                            store_sym(rt.cut, rt.cut_w, dst + i, rt.cut_w == 1 ? stage8[src + i] : stage16[src + i]);
                 }
                 __syncthreads();
             }
@@ -1479,11 +1523,15 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
     const uint32_t slot = blockIdx.x * WARPS + warp;
     if (slot >= a.nslots) return;
     const Job jb = a.jobs[slot];
+    if (!WT_IN(WT_BOUNDS_TABLE, jb.text, a.ntexts)) return;
     const TextInfo &t = a.texts[jb.text];
     if (!small_job(t, a.round, jb.n)) return;
     if ((KW == 1) != (jb.n <= 1024u)) return;        // the other instantiation takes it
     const RoundText rt = round_text(t, a.round);
     const uint32_t h = rt.h, rb = rt.rb, n = jb.n;
+    if (!WT_IN(WT_BOUNDS_TEXT, (uint64_t)jb.off + n, t.n + 1)) return;
+    if (!WT_IN(WT_BOUNDS_LEVEL, rt.c + h, t.L + 1)) return;
+    if (!WT_IN(WT_BOUNDS_SHARED, n, (uint32_t)(32 * NW) + 1)) return;
     const bool matrix = a.kind == WT_MATRIX;
     const uint8_t *in = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
     const uint32_t nj = (n + 1023u) / 1024u;          // rows of 32 words in use (1 .. KW)
@@ -1583,7 +1631,9 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
                 const uint32_t c = sm.cnt[q], from = sm.loc[q], to = sm.glo[q] - jb.off;
                 for (uint32_t i = 0; i < c; i += 64) {
                     const uint32_t len = min(64u, c - i);
-                    place_bits(sm.lvl2, to + i, extract_bits(sm.lvl, from + i, len), len);
+                    if (WT_IN(WT_BOUNDS_SHARED, (to + i + len - 1) >> 5, 32 * KW + 4) &&
+                        WT_IN(WT_BOUNDS_SHARED, ((from + i) >> 5) + 2, 32 * KW + 4))
+                        place_bits(sm.lvl2, to + i, extract_bits(sm.lvl, from + i, len), len);
                 }
             }
             __syncwarp();
@@ -1593,6 +1643,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
             uint64_t *lv = bv + (uint64_t)(rt.c + l) * t.W;
             const uint64_t off = jb.off, end = off + n;
             for (uint64_t d = (off >> 6) + lane; d <= (end - 1) >> 6; d += 32) {
+                if (!WT_IN(WT_BOUNDS_LEVEL, d, t.W)) break;
                 const uint64_t wb = d << 6;
                 const uint64_t lo = wb > off ? wb : off, hi = end < wb + 64 ? end : wb + 64;
                 const uint32_t blo = (uint32_t)(lo - wb);
@@ -1620,10 +1671,12 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
                 const uint32_t kz = z0 == 32u ? ~0u : (1u << z0) - 1u;
                 const uint32_t ko = z0 == 0u ? ~0u : (1u << (32u - z0)) - 1u;
                 const uint32_t d1 = zt + 32u * wj - zo;
+                const bool in_z = z0 == 0u || WT_IN(WT_BOUNDS_SHARED, (zo + z0 - 1u) >> 5, NW + 1);
+                const bool in_o = z0 == 32u || WT_IN(WT_BOUNDS_SHARED, (d1 + 31u - z0) >> 5, NW + 1);
                 for (uint32_t k = l + 1; k < h; ++k) {
                     const uint32_t x = cur[k][wj];
-                    place_bits(nxt[k], zo, compress_apply(x, kz, mz), z0);
-                    place_bits(nxt[k], d1, compress_apply(x, ko, mo), 32u - z0);
+                    if (in_z) place_bits(nxt[k], zo, compress_apply(x, kz, mz), z0);
+                    if (in_o) place_bits(nxt[k], d1, compress_apply(x, ko, mo), 32u - z0);
                     cur[k][wj] = 0;
                 }
             }
@@ -1798,3 +1851,53 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t in_w, cudaStream_t s)
 }
 
 }  // namespace wtg
+
+// ---------------------------------------------------------------------------
+// Report of the bounds checks (a build with -DWT_DEBUG_BOUNDS), see the header.
+
+#ifdef WT_DEBUG_BOUNDS
+namespace wtg {
+namespace {
+
+__global__ void k_bounds_selftest()
+{
+    // two checks with nothing behind them: the first fails, the second holds
+    const uint64_t one = threadIdx.x + 1u;
+    if (!WT_IN(WT_BOUNDS_SELFTEST, one, 1u)) {
+    }
+    if (!WT_IN(WT_BOUNDS_SELFTEST, one - 1u, 1u)) {
+    }
+}
+
+}  // namespace
+}  // namespace wtg
+#endif
+
+extern "C" wt_status wt_debug_bounds_read(wt_bounds_report *out, int reset)
+{
+    if (out == nullptr) return WT_ERR_INVALID_ARG;
+    *out = wt_bounds_report{};
+#ifdef WT_DEBUG_BOUNDS
+    if (cudaDeviceSynchronize() != cudaSuccess) return WT_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(out, wtg::g_bounds, sizeof(*out)) != cudaSuccess) return WT_ERR_CUDA;
+    out->enabled = 1;
+    if (reset) {
+        const wt_bounds_report zero{};
+        if (cudaMemcpyToSymbol(wtg::g_bounds, &zero, sizeof(zero)) != cudaSuccess) return WT_ERR_CUDA;
+    }
+#else
+    (void)reset;
+#endif
+    return WT_OK;
+}
+
+extern "C" wt_status wt_debug_bounds_selftest(void *stream)
+{
+#ifdef WT_DEBUG_BOUNDS
+    wtg::k_bounds_selftest<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>();
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+#else
+    (void)stream;
+    return WT_ERR_INVALID_ARG;
+#endif
+}

@@ -82,3 +82,18 @@ def test_host_build_argument_errors():
     assert call(p, wtg.WT_U8, n, 300, p, None, None, 0, fake_ws, need, None) == 1          # sigma > 2^8
     big = wtg.wt_host_workspace_size(wtg.WT_U32, n, 1 << 25)
     assert call(p, wtg.WT_U32, n, 1 << 25, p, None, None, 0, fake_ws, big, None) == 1      # WT beyond 2^24
+
+
+def test_bounds_report_of_the_default_build():
+    """The default build compiles no bounds checks: the report says so and the
+    self-test is refused, both without touching a device."""
+    r = wtg.wt_debug_bounds_read()
+    assert r == {"enabled": False, "failures": 0, "site": "selftest", "index": 0, "bound": 0}
+    assert wtg.lib().wt_debug_bounds_selftest(None) == 1
+
+
+def test_bounds_checked_build_compiles_and_exports_the_boundary():
+    path = _native.build(debug_bounds=True)
+    assert path == _native.LIB_PATH_DBG and path != _native.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert set(declared_functions()) <= set(re.findall(r"\bT\s+(\w+)", out))
