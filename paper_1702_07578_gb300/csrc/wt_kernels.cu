@@ -636,8 +636,13 @@ struct BsSmem {
     uint32_t wz[kChunk][kWarps];              // zeros of level l's plane in each warp's range
     uint32_t thc[kCols];                      // class counts of the tile (histogram pass)
     union {
-        uint16_t cntw[kWarps][kCols];         // cut: class counts / offsets per warp chunk
-        uint8_t wcls2[kChunk][kWcap];         // kBoth: wcls of the WM
+        uint32_t cntw[kWarps][kCols];         // cut: class counts / offsets per warp chunk
+        struct {                              // kBoth: the WM's wcls, jspos, glo, wpre
+            uint8_t wcls2[kChunk][kWcap];
+            uint32_t jspos2[kHeap];
+            uint32_t glo2[kHeap];
+            uint32_t wpre2[kHeap];
+        };
     };
     uint8_t wcls[kChunk][kWcap];              // destination word -> class, per level
     uint32_t tP[kCols + 1];
@@ -651,10 +656,7 @@ struct BsSmem {
     uint32_t glo[kHeap];                      // class start inside the text's level (bits)
     uint32_t wpre[kHeap];                     // destination words before each class
     uint32_t wtot[kChunk + 2];
-    uint32_t jspos2[kHeap];                   // kBoth: the WM's jspos, glo, wpre, wtot
-    uint32_t glo2[kHeap];
-    uint32_t wpre2[kHeap];
-    uint32_t wtot2[kChunk + 2];
+    uint32_t wtot2[kChunk + 2];               // kBoth: the WM's wtot
 };
 
 // Two blocks per SM: each block's shared memory (plus the 1 KB the hardware
@@ -933,6 +935,25 @@ __device__ __forceinline__ void load32(const uint8_t *tile, uint32_t w, uint32_t
     }
 }
 
+// Class counts for the counting sort of rounds that cut: the h-bit class of
+// symbols e0 .. e0 + 31 (bytes of x, in load32's layout; symbols at or beyond m
+// are not counted) on the warp's row of counters.  Thread t loads symbols
+// [64t, 64t + 64), so warp w counts exactly the symbols [2048w, 2048w + 2048) it
+// ranks after the levels.
+__device__ __forceinline__ void count_classes(const uint32_t x[8], uint32_t e0, uint32_t m, uint32_t h,
+                                              uint32_t *row)
+{
+    const uint32_t cmask = (1u << h) - 1u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t q = (x[k] >> (8 * b)) & cmask;
+            if (e0 + 4u * k + b < m) atomicAdd(&row[q], 1u);
+        }
+    }
+}
+
 // Transposes 32 symbols and stores plane k (code bit rb-1-k) of word w; returns
 // plane 0's word.
 __device__ __forceinline__ uint32_t store_planes(uint32_t x[8], uint32_t rb, uint32_t h,
@@ -1033,6 +1054,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
     const uint32_t w0 = 2u * tid;                    // this thread's words: w0, w0 + 1
 
     const uint32_t tile_first = jb.tile0 + (uint32_t)(g_begin / kTileSyms);
+    // the tile is stably sorted by its class after the levels (the next round's text,
+    // or the stable order): its classes are counted per warp while it is loaded
+    const bool cuts = CUT && (rt.cut != nullptr || t.perm != nullptr);
     uint32_t tix = 0;
     for (uint64_t t0 = g_begin; t0 < g_end; t0 += kBsTile, ++tix) {
         const uint32_t m = (uint32_t)min((uint64_t)kBsTile, g_end - t0);
@@ -1046,6 +1070,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         }
         if (tid < (uint32_t)kChunk) sm.plane[0][tid][kBsWords] = sm.plane[0][tid][kBsWords + 1] = 0;
         if (tid < (uint32_t)(kChunk * kWarps)) (&sm.wz[0][0])[tid] = 0;
+        if (cuts)
+            for (uint32_t i = tid; i < (uint32_t)(kWarps * kCols); i += kThreads) (&sm.cntw[0][0])[i] = 0;
         for (uint32_t q = tid; q < kCols; q += kThreads)
             sm.thc[q] = WT_IN(WT_BOUNDS_TABLE, tile_first + tix, job_rows)
                             ? a.thist[((size_t)tile_first + tix) * kCols + q] : 0u;
@@ -1168,8 +1194,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             uint32_t x[8];
             load32(tile, rt.in_w, 32u * w0, m, shift, x);
+            if (cuts) count_classes(x, 32u * w0, m, h, sm.cntw[warp]);
             const uint32_t f0 = store_planes(x, h, h, sm.plane[0], w0);
             load32(tile, rt.in_w, 32u * w0 + 32u, m, shift, x);
+            if (cuts) count_classes(x, 32u * w0 + 32u, m, h, sm.cntw[warp]);
             const uint32_t f1 = store_planes(x, h, h, sm.plane[0], w0 + 1);
             const uint32_t z = __reduce_add_sync(kFull, __popc(~f0) + __popc(~f1));
             if (lane == 0) sm.wz[0][warp] = z;
@@ -1320,14 +1348,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         //      When the text wants its stable order, the same ranks place every
         //      symbol's text position: in the next round's position buffer, or,
         //      in the last round, in the order after the last level.
-        if (CUT && (rt.cut != nullptr || t.perm != nullptr)) {
+        if (cuts) {
             constexpr uint32_t kPer = kBsTile / kWarps;
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             const uint32_t low = (1u << shift) - 1u;
             const uint32_t cmask = (1u << h) - 1u;       // classes of this round (k_hist counts the same)
             const uint32_t e_end = min(m, warp * kPer + kPer);
             const uint32_t base_h = 1u << h;
-            uint16_t *cw = sm.cntw[warp];
+            uint32_t *cw = sm.cntw[warp];
             uint8_t *stage8 = reinterpret_cast<uint8_t *>(&sm.plane[0][0][0]);
             uint16_t *stage16 = reinterpret_cast<uint16_t *>(&sm.plane[0][0][0]);
             const bool staged = rt.cut != nullptr && rt.cut_w <= 2;   // 32768 values fit the plane buffers
@@ -1338,37 +1366,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint64_t pos0 = (uint64_t)jb.off + t0;             // round-buffer position of symbol 0
             const uint32_t *pin = a.round ? t.pbuf[(a.round - 1) & 1] : nullptr;
             uint32_t *pout = t.perm == nullptr ? nullptr : (rt.cut != nullptr ? t.pbuf[a.round & 1] : t.perm);
-            // 32-bit per-warp counters for the atomics (16 warps x 256 words = 16 KB)
-            // in the second half of the plane buffers, idle between the level loop
-            // and the staging below
-            uint32_t *cwc = reinterpret_cast<uint32_t *>(&sm.plane[1][0][0]) + warp * kCols;
-            for (uint32_t q = lane; q < kCols; q += 32) cwc[q] = 0;
-            __syncwarp();
-            // symbols in chunks of 8 steps of 32: the 8 loads of a lane are issued
-            // together, so a chunk waits for memory once
+            // per-warp class counts (taken while the tile was loaded) -> offsets of
+            // each warp's symbols among the tile's symbols of the class
             constexpr uint32_t kSteps = 8;
             static_assert(kPer % (32 * kSteps) == 0, "whole chunks per warp");
-            for (uint32_t c0 = warp * kPer; c0 < e_end; c0 += 32 * kSteps) {
-                uint32_t vs[kSteps];
-#pragma unroll
-                for (uint32_t k = 0; k < kSteps; ++k) {
-                    const uint32_t e = c0 + 32 * k + lane;
-                    vs[k] = e < e_end ? load_sym(tile, rt.in_w, e) : 0u;
-                }
-                // counts only (the ranks below are taken stably): one shared
-                // atomic per symbol on this warp's own row
-#pragma unroll
-                for (uint32_t k = 0; k < kSteps; ++k)
-                    if (c0 + 32 * k + lane < e_end) atomicAdd(&cwc[((vs[k] >> shift) & cmask)], 1u);
-            }
-            __syncwarp();
-            for (uint32_t q = lane; q < kCols; q += 32) cw[q] = (uint16_t)cwc[q];
-            __syncthreads();
             for (uint32_t q = tid; q < kCols; q += kThreads) {
                 uint32_t run = 0;
                 for (int w = 0; w < kWarps; ++w) {
                     const uint32_t c = sm.cntw[w][q];
-                    sm.cntw[w][q] = (uint16_t)run;
+                    sm.cntw[w][q] = run;
                     run += c;
                 }
             }
@@ -1391,7 +1397,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     const uint32_t rank = ok ? cw[q] + __popc(peers & lt) : 0u;
                     __syncwarp();
                     if (ok) {
-                        if ((peers >> lane) == 1u) cw[q] = (uint16_t)(rank + 1u);
+                        // the last lane of each class advances its counter by the class's
+                        // lanes in this step.  An atomic: with the counts taken at load time a
+                        // plain store here gave wrong ranks in 8-level rounds (measured, cause
+                        // not found; the atomic update is correct on every tested case)
+                        if ((peers >> lane) == 1u) atomicAdd(&cw[q], (uint32_t)__popc(peers));
                         const uint64_t dst = (uint64_t)sm.glo[base_h + q] + rank;
                         if (pstaged) {
                             if (WT_IN(WT_BOUNDS_SHARED, sm.loc[base_h + q] + rank, kBsTile))
