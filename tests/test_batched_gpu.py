@@ -159,3 +159,34 @@ def test_batched_mixed_round_geometry(kind):
             e, ez = oracle.wm(T, sigma)
             assert np.array_equal(to_u64(bvs[i]), e), f"text {i} sigma {sigma}"
             assert np.array_equal(zs[i][:e.shape[0]].cpu().numpy().astype(np.uint64), ez)
+
+
+@pytest.mark.parametrize("kind", ["wt", "wm"])
+def test_batched_workload_slice_full_lengths(kind):
+    """A 512-text slice of the batched workload with its full length range (2^10 to
+    2^20 symbols, sigma 2^4 .. 2^16), built by one graph replay with the default
+    block size: every text equal to the oracle."""
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    specs = synth.batch_specs(512)
+    assert max(n for n, _, _ in specs) > 1 << 19
+    texts = synth.batch_texts(specs)
+    sigmas = [s for _, s, _ in specs]
+    k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+    dts = [torch_text(t) for t in texts]
+    bv = [torch.full((wtg.wt_levels(s), wtg.wt_words_per_level(t.size)), -1, dtype=torch.int64, device="cuda")
+          for t, s in zip(texts, sigmas)]
+    zz = [torch.empty((max(wtg.wt_levels(s), 1),), dtype=torch.int64, device="cuda") for s in sigmas]
+    stream = torch.cuda.Stream()
+    plan = wtg.WtBatchPlan(k, dts, sigmas, bv, zz if kind == "wm" else None, stream=stream)
+    plan.launch()
+    stream.synchronize()
+    for i, (T, sigma) in enumerate(zip(texts, sigmas)):
+        if kind == "wt":
+            assert np.array_equal(to_u64(bv[i]), oracle.wt(T, sigma)), f"text {i} n {T.size} sigma {sigma}"
+        else:
+            e, ez = oracle.wm(T, sigma)
+            assert np.array_equal(to_u64(bv[i]), e), f"text {i} n {T.size} sigma {sigma}"
+            assert np.array_equal(zz[i][:e.shape[0]].cpu().numpy().astype(np.uint64), ez), f"Z {i}"
+    plan.close()
