@@ -1055,8 +1055,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
 
     const uint32_t tile_first = jb.tile0 + (uint32_t)(g_begin / kTileSyms);
     // the tile is stably sorted by its class after the levels (the next round's text,
-    // or the stable order): its classes are counted per warp while it is loaded
+    // or the stable order).  In rounds of fewer than 8 levels its classes are counted
+    // per warp while it is loaded; 8-level rounds count them after the levels, where
+    // a second read of the tile costs less than the atomic rank updates below
     const bool cuts = CUT && (rt.cut != nullptr || t.perm != nullptr);
+    const bool load_count = cuts && h < (uint32_t)kChunk;
     uint32_t tix = 0;
     for (uint64_t t0 = g_begin; t0 < g_end; t0 += kBsTile, ++tix) {
         const uint32_t m = (uint32_t)min((uint64_t)kBsTile, g_end - t0);
@@ -1070,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
         }
         if (tid < (uint32_t)kChunk) sm.plane[0][tid][kBsWords] = sm.plane[0][tid][kBsWords + 1] = 0;
         if (tid < (uint32_t)(kChunk * kWarps)) (&sm.wz[0][0])[tid] = 0;
-        if (cuts)
+        if (load_count)
             for (uint32_t i = tid; i < (uint32_t)(kWarps * kCols); i += kThreads) (&sm.cntw[0][0])[i] = 0;
         for (uint32_t q = tid; q < kCols; q += kThreads)
             sm.thc[q] = WT_IN(WT_BOUNDS_TABLE, tile_first + tix, job_rows)
@@ -1194,10 +1197,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint8_t *tile = in_base + (size_t)t0 * rt.in_w;
             uint32_t x[8];
             load32(tile, rt.in_w, 32u * w0, m, shift, x);
-            if (cuts) count_classes(x, 32u * w0, m, h, sm.cntw[warp]);
+            if (load_count) count_classes(x, 32u * w0, m, h, sm.cntw[warp]);
             const uint32_t f0 = store_planes(x, h, h, sm.plane[0], w0);
             load32(tile, rt.in_w, 32u * w0 + 32u, m, shift, x);
-            if (cuts) count_classes(x, 32u * w0 + 32u, m, h, sm.cntw[warp]);
+            if (load_count) count_classes(x, 32u * w0 + 32u, m, h, sm.cntw[warp]);
             const uint32_t f1 = store_planes(x, h, h, sm.plane[0], w0 + 1);
             const uint32_t z = __reduce_add_sync(kFull, __popc(~f0) + __popc(~f1));
             if (lane == 0) sm.wz[0][warp] = z;
@@ -1366,10 +1369,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
             const uint64_t pos0 = (uint64_t)jb.off + t0;             // round-buffer position of symbol 0
             const uint32_t *pin = a.round ? t.pbuf[(a.round - 1) & 1] : nullptr;
             uint32_t *pout = t.perm == nullptr ? nullptr : (rt.cut != nullptr ? t.pbuf[a.round & 1] : t.perm);
-            // per-warp class counts (taken while the tile was loaded) -> offsets of
-            // each warp's symbols among the tile's symbols of the class
+            // symbols in chunks of 8 steps of 32: the 8 loads of a lane are issued
+            // together, so a chunk waits for memory once
             constexpr uint32_t kSteps = 8;
             static_assert(kPer % (32 * kSteps) == 0, "whole chunks per warp");
+            if (!load_count) {
+                // 8-level rounds: the counts of each warp's symbols, read again, on
+                // 32-bit counters in the second half of the plane buffers (16 warps x
+                // 256 words = 16 KB, idle between the level loop and the staging)
+                uint32_t *cwc = reinterpret_cast<uint32_t *>(&sm.plane[1][0][0]) + warp * kCols;
+                for (uint32_t q = lane; q < kCols; q += 32) cwc[q] = 0;
+                __syncwarp();
+                for (uint32_t c0 = warp * kPer; c0 < e_end; c0 += 32 * kSteps) {
+                    uint32_t vs[kSteps];
+#pragma unroll
+                    for (uint32_t k = 0; k < kSteps; ++k) {
+                        const uint32_t e = c0 + 32 * k + lane;
+                        vs[k] = e < e_end ? load_sym(tile, rt.in_w, e) : 0u;
+                    }
+#pragma unroll
+                    for (uint32_t k = 0; k < kSteps; ++k)
+                        if (c0 + 32 * k + lane < e_end) atomicAdd(&cwc[((vs[k] >> shift) & cmask)], 1u);
+                }
+                __syncwarp();
+                for (uint32_t q = lane; q < kCols; q += 32) cw[q] = cwc[q];
+                __syncthreads();
+            }
+            // per-warp class counts -> offsets of each warp's symbols among the
+            // tile's symbols of the class
             for (uint32_t q = tid; q < kCols; q += kThreads) {
                 uint32_t run = 0;
                 for (int w = 0; w < kWarps; ++w) {
@@ -1398,10 +1425,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_bs(RoundArgs a)
                     __syncwarp();
                     if (ok) {
                         // the last lane of each class advances its counter by the class's
-                        // lanes in this step.  An atomic: with the counts taken at load time a
-                        // plain store here gave wrong ranks in 8-level rounds (measured, cause
-                        // not found; the atomic update is correct on every tested case)
-                        if ((peers >> lane) == 1u) atomicAdd(&cw[q], (uint32_t)__popc(peers));
+                        // lanes in this step.  With the counts taken at load time this is an
+                        // atomic: a plain store there gave wrong ranks in the normal build
+                        // (measured; cause not found), while every build with the atomic and
+                        // every build counting after the levels with the plain store was right
+                        if ((peers >> lane) == 1u) {
+                            if (load_count) atomicAdd(&cw[q], (uint32_t)__popc(peers));
+                            else cw[q] = rank + 1u;
+                        }
                         const uint64_t dst = (uint64_t)sm.glo[base_h + q] + rank;
                         if (pstaged) {
                             if (WT_IN(WT_BOUNDS_SHARED, sm.loc[base_h + q] + rank, kBsTile))
