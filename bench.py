@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (the third k_build_bs launch)
-    "91586b79c4dc34fa007244c981b795d3ebd2031ad154c4dcc540b2f9a6ba6d7a": {"dram_bytes": 313401856 + 224912640,
+    "1669892f3f0f8691e83a1ce0cdd45d71f2c03560e95937020162bbc0ec9323fd": {"dram_bytes": 313187072 + 225069568,
                                                                          "n": 1 << 28},
 }
 
