@@ -554,8 +554,10 @@ def batched_block(args, pg, world, steps=None):
     plans, outs = {}, {}
     for kind in (wtg.WT_TREE, wtg.WT_MATRIX):
         bv, zz = outputs()
-        best = wtg.wt_autotune_batched(kind, texts, sigmas, bv, zz if kind else None, stream=stream)
-        plans[kind] = (wtg.WtBatchPlan(kind, texts, sigmas, bv, zz if kind else None, stream=stream), best)
+        spb = args.symbols_per_block
+        best = spb or wtg.wt_autotune_batched(kind, texts, sigmas, bv, zz if kind else None, stream=stream)
+        plans[kind] = (wtg.WtBatchPlan(kind, texts, sigmas, bv, zz if kind else None, stream=stream,
+                                       symbols_per_block=spb), best)
         outs[kind] = (bv, zz)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -574,6 +576,14 @@ def batched_block(args, pg, world, steps=None):
         stream.synchronize()
     ms = max_over_ranks(pg, e0.elapsed_time(e1) / steps)
     value = world * 2 * total / (ms / 1e3)
+    config = {"workload": f"{count} texts, length floor(2^(10+10u)), sigma in {{2^4,2^8,2^12,2^16}}, "
+                          f"uint16, Zipf(0.8) over per-text permutations",
+              "symbols": total, "builds_per_step": 2 * count,
+              "symbols_per_block": {"wt": plans[0][1], "wm": plans[1][1]},
+              "launch": "one CUDA graph replay per kind per step"}
+    if args.no_plain:                  # profiler runs: the graph replays only
+        return {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps, "config": config,
+                "roofline": batched_roofline(texts_h, sigmas, ms)}
 
     # the same texts, one plain build per text (per-text workspace, resident inputs)
     ws = [torch.empty((max(wtg.wt_workspace_size(wtg.WT_TREE, 2, t.numel(), sg),
@@ -606,11 +616,7 @@ def batched_block(args, pg, world, steps=None):
     assert same, "batched output differs from the per-text builds"
     plain_value = world * 2 * total / (plain_ms / 1e3)
     return {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "config": {"workload": f"{count} texts, length floor(2^(10+10u)), sigma in {{2^4,2^8,2^12,2^16}}, "
-                                   f"uint16, Zipf(0.8) over per-text permutations",
-                       "symbols": total, "builds_per_step": 2 * count,
-                       "symbols_per_block": {"wt": plans[0][1], "wm": plans[1][1]},
-                       "launch": "one CUDA graph replay per kind per step"},
+            "config": config,
             "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
                       "device_ms_per_step": plain_ev, "host_wall_ms_per_step": plain_wall * 1e3,
                       "launch": f"{2 * count} wt_build/wm_build calls per step"},
@@ -975,6 +981,10 @@ def main(argv=None):
                              "large"])
     ap.add_argument("--queries", type=int, default=1 << 24)
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--symbols-per-block", type=int, default=0,
+                    help="batched: this many symbols per build block instead of the autotuner's choice")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batched: leave out the per-text builds (for profiler captures of the replays)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=None,
                     help="served: one run at this many arrivals per second (default: a sweep "
