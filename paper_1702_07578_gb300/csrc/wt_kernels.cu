@@ -429,6 +429,11 @@ __global__ void __launch_bounds__(kHistThreads, LC ? 6 : 8) k_hist(RoundArgs a)
     const uint32_t top4 = top * 0x01010101u;
     const uint32_t tile_first = jb.tile0 + (uint32_t)(g0 / kTileSyms);
     uint32_t gsum = 0;                                   // running group count of column threadIdx.x
+    // byte rounds over all 256 classes whose symbols cannot be out of range (the
+    // one round of sigma = 2^8, or an 8-level last round of a larger alphabet): the
+    // class is the byte itself
+    const bool fullbyte = shift == 0 && mask == 0xffu && top == 0 && !check;
+    uint32_t *colp = wh + col;
     for (uint32_t i = threadIdx.x; i < (uint32_t)kCols * stride; i += kHistThreads) wh[i] = 0;
     __syncthreads();
     // one tile (kTileSyms symbols) at a time; a tile's row is the difference of
@@ -452,13 +457,26 @@ __global__ void __launch_bounds__(kHistThreads, LC ? 6 : 8) k_hist(RoundArgs a)
                 for (int u = 0; u < 4; ++u) {
                     if (k0 + (uint64_t)u * kHistThreads >= nchunks) break;
                     const uint32_t words[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+                    if (LC && fullbyte) {
+                        // the class is the byte: one byte permute and one address per
+                        // symbol (2^30 bytes: 0.286 against 0.324 ms)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t x = words[j];
-                        bad |= (x & top4) != 0u;
-                        if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t x = words[j];
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) atomicAdd(&mine[stride * ((x >> (8 * b + shift)) & mask) + col], 1u);
+                            for (int b = 0; b < 4; ++b)
+                                atomicAdd(colp + (__byte_perm(x, 0u, 0x4440u + (uint32_t)b) << 5), 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t x = words[j];
+                            bad |= (x & top4) != 0u;
+                            if (check) bad |= __vcmpgeu4(x, sig * 0x01010101u) != 0u;
+#pragma unroll
+                            for (int b = 0; b < 4; ++b)
+                                atomicAdd(&mine[stride * ((x >> (8 * b + shift)) & mask) + col], 1u);
+                        }
                     }
                 }
             }
