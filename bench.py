@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (the third k_build_bs launch)
-    "1669892f3f0f8691e83a1ce0cdd45d71f2c03560e95937020162bbc0ec9323fd": {"dram_bytes": 313187072 + 225069568,
+    "34cde1626192c4c9a3a4b2a0ff158dd75e060eff6ee4458b75b5953188231a5d": {"dram_bytes": 313163520 + 224944896,
                                                                          "n": 1 << 28},
 }
 
