@@ -107,6 +107,7 @@ __device__ __forceinline__ RoundText round_text(const TextInfo &t, uint32_t r)
 constexpr uint32_t kSmallWords = 4;                  // words per lane of the warp build
 constexpr int kSmallWarps = 8;                        // warps per block of the 4-row instantiation
 constexpr int kTinyWarps = 16;                        // warps per block of the 1-row instantiation
+constexpr uint32_t kLaneJob = 256;                    // small jobs up to this size: one thread each
 static_assert(kSmallJob == 32 * 32 * kSmallWords, "a small job is one warp's 32 x 32 x kSmallWords bits");
 
 __device__ __forceinline__ bool small_job(const TextInfo &t, uint32_t round, uint64_t n)
@@ -1539,6 +1540,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
     const TextInfo &t = a.texts[jb.text];
     if (!small_job(t, a.round, jb.n)) return;
     if ((KW == 1) != (jb.n <= 1024u)) return;        // the other instantiation takes it
+    if (jb.n <= kLaneJob) return;                     // one thread each (k_build_lane)
     const RoundText rt = round_text(t, a.round);
     const uint32_t h = rt.h, rb = rt.rb, n = jb.n;
     if (!WT_IN(WT_BOUNDS_TEXT, (uint64_t)jb.off + n, t.n + 1)) return;
@@ -1697,6 +1699,105 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The smallest jobs (at most kLaneJob symbols, last round of their text): one
+// thread builds a whole job.  Most of them are the wavelet tree's subtrees of
+// short texts with large alphabets, a few dozen symbols each, where a warp would
+// spend its instructions on 32 mostly empty words.  Per level l the thread counts
+// its symbols' l-bit prefixes, takes the node starts by an exclusive scan of the
+// counts (id order for the WT, reversed prefixes for the WM: Sec. 3.1 / 5.1), and
+// sets every symbol's level bit at its node's next position, in text order (the
+// stable scatter of Alg. 1).  Element k of lane i's arrays is at index 32k + i, so
+// that the lanes of a warp touch consecutive addresses.
+
+namespace {
+
+constexpr int kLaneWarps = 4;                         // warps per block of k_build_lane
+constexpr uint32_t kLaneWords = kLaneJob / 32 + 2;    // bit buffer words per lane (+ two spare words)
+
+struct LaneSmem {                                     // per warp
+    uint8_t sym[kLaneJob * 32];                       // the job's symbols in text order
+    uint16_t ctr[(kCols / 2) * 32];                   // node counters of level l (2^l <= 128)
+    uint32_t bits[kLaneWords * 32];                   // the level's bits in node order
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(kLaneWarps * 32) k_build_lane(RoundArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    LaneSmem &sm = reinterpret_cast<LaneSmem *>(smem_raw)[warp];
+    const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= a.nslots) return;
+    const Job jb = a.jobs[slot];
+    if (jb.n > kLaneJob) return;
+    if (!WT_IN(WT_BOUNDS_TABLE, jb.text, a.ntexts)) return;
+    const TextInfo &t = a.texts[jb.text];
+    if (!small_job(t, a.round, jb.n)) return;
+    const RoundText rt = round_text(t, a.round);
+    const uint32_t h = rt.h, n = jb.n;
+    if (!WT_IN(WT_BOUNDS_TEXT, (uint64_t)jb.off + n, t.n + 1)) return;
+    if (!WT_IN(WT_BOUNDS_LEVEL, rt.c + h, t.L + 1)) return;
+    const bool matrix = a.kind == WT_MATRIX;
+    const uint8_t *in = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
+    // the last round's symbols have h <= 8 code bits (rb == h); like the warp
+    // kernel, only their low h bits are used, so every prefix indexes a node of
+    // its level and every position stays below n
+    const uint32_t hmask = (1u << h) - 1u;
+    for (uint32_t i = 0; i < n; ++i) sm.sym[32u * i + lane] = (uint8_t)(load_sym(in, rt.in_w, i) & hmask);
+    for (uint32_t l = 0; l < h; ++l) {
+        const uint32_t base = 1u << l, sh = h - l;
+        for (uint32_t q = 0; q < base; ++q) sm.ctr[32u * q + lane] = 0;
+        for (uint32_t i = 0; i < n; ++i) ++sm.ctr[32u * (sm.sym[32u * i + lane] >> sh) + lane];
+        uint32_t run = 0;
+        for (uint32_t k = 0; k < base; ++k) {
+            const uint32_t q = matrix ? rev_bits(k, l) : k;
+            const uint32_t c = sm.ctr[32u * q + lane];
+            sm.ctr[32u * q + lane] = (uint16_t)run;
+            run += c;
+        }
+        const uint32_t nw = (n + 31u) / 32u;
+        for (uint32_t w = 0; w < nw + 2u; ++w) sm.bits[32u * w + lane] = 0;
+        uint32_t z = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint32_t v = sm.sym[32u * i + lane];
+            const uint32_t q = v >> sh, b = (v >> (sh - 1u)) & 1u;
+            const uint32_t d = sm.ctr[32u * q + lane];
+            sm.ctr[32u * q + lane] = (uint16_t)(d + 1u);
+            sm.bits[32u * (d >> 5) + lane] |= b << (d & 31u);
+            z += b ^ 1u;
+        }
+        if (matrix) t.zeros[rt.c + l] = z;              // Z[c + l]: zeros of level l (the whole text)
+        // the job's bits are the range [off, off + n) of level c + l
+        uint64_t *lv = t.bv + (uint64_t)(rt.c + l) * t.W;
+        const uint64_t off = jb.off, end = off + n;
+        for (uint64_t dw = off >> 6; dw <= (end - 1) >> 6; ++dw) {
+            if (!WT_IN(WT_BOUNDS_LEVEL, dw, t.W)) break;
+            const uint64_t wb = dw << 6;
+            const uint64_t lo = wb > off ? wb : off, hi = end < wb + 64 ? end : wb + 64;
+            const uint32_t blo = (uint32_t)(lo - wb);
+            uint32_t bhi = (uint32_t)(hi - wb);
+            const uint32_t src = (uint32_t)(lo - off), len = bhi - blo;
+            const uint32_t w0 = src >> 5, s0 = src & 31u;
+            const uint64_t pair = ((uint64_t)sm.bits[32u * (w0 + 1u) + lane] << 32) | sm.bits[32u * w0 + lane];
+            uint64_t val = pair >> s0;
+            if (s0) val |= (uint64_t)sm.bits[32u * (w0 + 2u) + lane] << (64u - s0);
+            if (len < 64u) val &= (1ull << len) - 1ull;
+            val <<= blo;
+            if (end == t.n) bhi = 64;                  // bits past n belong to the last job
+            if (blo == 0 && bhi == 64) {
+                lv[dw] = val;
+            } else {
+                const uint64_t msk = (bhi == 64 ? ~0ull : ((1ull << bhi) - 1ull)) & ~((1ull << blo) - 1ull);
+                atomicAnd(reinterpret_cast<unsigned long long *>(lv + dw), ~msk);
+                atomicOr(reinterpret_cast<unsigned long long *>(lv + dw), val);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 cudaError_t configure_kernels()
@@ -1707,6 +1808,9 @@ cudaError_t configure_kernels()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_build_small<kSmallWords, kSmallWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(SmallSmem<kSmallWords>) * kSmallWarps));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_build_lane, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(LaneSmem) * kLaneWarps));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_hist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
     if (e != cudaSuccess) return e;
@@ -1854,12 +1958,14 @@ cudaError_t launch_round(const RoundArgs &a, uint32_t in_w, cudaStream_t s)
     }
     if (a.any_small && a.kind != kBoth)           // kBoth has no small jobs
     {
+        k_build_lane<<<(a.nslots + kLaneWarps * 32 - 1) / (kLaneWarps * 32), kLaneWarps * 32,
+                       sizeof(LaneSmem) * kLaneWarps, s>>>(a);
         k_build_small<1, kTinyWarps><<<(a.nslots + kTinyWarps - 1) / kTinyWarps, kTinyWarps * 32,
                                       sizeof(SmallSmem<1>) * kTinyWarps, s>>>(a);
         k_build_small<kSmallWords, kSmallWarps><<<(a.nslots + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32,
                                                   sizeof(SmallSmem<kSmallWords>) * kSmallWarps, s>>>(a);
     }
-    if (prof) profile_mark(0, false, s, (a.any_small && a.kind != kBoth) ? 3 : 1);
+    if (prof) profile_mark(0, false, s, (a.any_small && a.kind != kBoth) ? 4 : 1);
     return cudaGetLastError();
 }
 
