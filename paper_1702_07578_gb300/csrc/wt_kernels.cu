@@ -1713,12 +1713,16 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
 
 namespace {
 
-constexpr int kLaneWarps = 4;                         // warps per block of k_build_lane
+constexpr int kLaneWarps = 2;                         // warps per block of k_build_lane (13.6 KB of shared
+                                                      // memory per warp: 8 blocks, 16 warps per SM)
 constexpr uint32_t kLaneWords = kLaneJob / 32 + 2;    // bit buffer words per lane (+ two spare words)
 
 struct LaneSmem {                                     // per warp
     uint8_t sym[kLaneJob * 32];                       // the job's symbols in text order
-    uint16_t ctr[(kCols / 2) * 32];                   // node counters of level l (2^l <= 128)
+    uint8_t ctr[(kCols / 2) * 32];                    // node counters of level l (2^l <= 128): positions
+                                                      // below n <= 256 fit in a byte; a count of 256 (one
+                                                      // node holding every symbol) wraps to 0, which is
+                                                      // then the start of empty nodes only
     uint32_t bits[kLaneWords * 32];                   // the level's bits in node order
 };
 
@@ -1755,7 +1759,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_build_lane(RoundArgs a)
         for (uint32_t k = 0; k < base; ++k) {
             const uint32_t q = matrix ? rev_bits(k, l) : k;
             const uint32_t c = sm.ctr[32u * q + lane];
-            sm.ctr[32u * q + lane] = (uint16_t)run;
+            sm.ctr[32u * q + lane] = (uint8_t)run;
             run += c;
         }
         const uint32_t nw = (n + 31u) / 32u;
@@ -1765,7 +1769,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_build_lane(RoundArgs a)
             const uint32_t v = sm.sym[32u * i + lane];
             const uint32_t q = v >> sh, b = (v >> (sh - 1u)) & 1u;
             const uint32_t d = sm.ctr[32u * q + lane];
-            sm.ctr[32u * q + lane] = (uint16_t)(d + 1u);
+            sm.ctr[32u * q + lane] = (uint8_t)(d + 1u);
             sm.bits[32u * (d >> 5) + lane] |= b << (d & 31u);
             z += b ^ 1u;
         }
