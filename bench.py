@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (the third k_build_bs launch)
-    "34cde1626192c4c9a3a4b2a0ff158dd75e060eff6ee4458b75b5953188231a5d": {"dram_bytes": 313163520 + 224944896,
+    "5beba8e2f087c155c1e30a6d005c5f471277becd895731ddd7ef5cf875f0e843": {"dram_bytes": 313189120 + 225406208,
                                                                          "n": 1 << 28},
 }
 
