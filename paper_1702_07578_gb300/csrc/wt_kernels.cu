@@ -1550,6 +1550,16 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_build_small(RoundArgs a)
     const uint8_t *in = static_cast<const uint8_t *>(rt.in) + (size_t)jb.off * rt.in_w;
     const uint32_t nj = (n + 1023u) / 1024u;          // rows of 32 words in use (1 .. KW)
     const uint32_t nwu = 32u * nj;                    // words in use; word nwu takes overflow bits
+    if (a.round == 0) {                               // symbols >= sigma, as in the histogram pass
+        const bool check = t.sigma < (1ull << t.L);
+        const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
+        bool bad = false;
+        for (uint32_t i = lane; i < n; i += 32) {
+            const uint32_t v = load_sym(in, rt.in_w, i);
+            bad |= (check && v >= sig) || (t.L < 32 && (v >> t.L) != 0);
+        }
+        if (__any_sync(kFull, bad) && lane == 0) atomicCAS(&a.ctl->status, 0u, (uint32_t)WT_ERR_SYMBOL_RANGE);
+    }
 
     // ---- clear, load and transpose (plane k = code bit rb-1-k), class counts
     for (uint32_t k = 0; k < 2 * kChunk; ++k)
@@ -1750,7 +1760,18 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_build_lane(RoundArgs a)
     // kernel, only their low h bits are used, so every prefix indexes a node of
     // its level and every position stays below n
     const uint32_t hmask = (1u << h) - 1u;
-    for (uint32_t i = 0; i < n; ++i) sm.sym[32u * i + lane] = (uint8_t)(load_sym(in, rt.in_w, i) & hmask);
+    // first round: symbols >= sigma (or beyond the L code bits) are reported, as in
+    // the histogram pass, which has no group of a small job to look at
+    const bool first = a.round == 0;
+    const bool check = first && t.sigma < (1ull << t.L);
+    const uint32_t sig = (uint32_t)min(t.sigma, (uint64_t)0xffffffffu);
+    bool bad = false;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t v = load_sym(in, rt.in_w, i);
+        bad |= (check && v >= sig) || (first && t.L < 32 && (v >> t.L) != 0);
+        sm.sym[32u * i + lane] = (uint8_t)(v & hmask);
+    }
+    if (bad) atomicCAS(&a.ctl->status, 0u, (uint32_t)WT_ERR_SYMBOL_RANGE);
     for (uint32_t l = 0; l < h; ++l) {
         const uint32_t base = 1u << l, sh = h - l;
         for (uint32_t q = 0; q < base; ++q) sm.ctr[32u * q + lane] = 0;

@@ -67,3 +67,45 @@ def test_many_tiny_subtrees_of_a_large_alphabet():
         bm, z = gpu_wm(T, 1 << 16)
         em, ez = oracle.wm(T, 1 << 16)
         assert np.array_equal(bm, em) and np.array_equal(z, ez), gen
+
+
+def _status_after_build(kind, T, sigma):
+    import torch
+
+    import paper_1702_07578_gb300 as wtg
+    from tests.gpu_util import torch_text
+    t = torch_text(T)
+    k = wtg.WT_TREE if kind == "wt" else wtg.WT_MATRIX
+    ws = torch.empty((wtg.wt_workspace_size(k, T.dtype.itemsize, t.numel(), sigma),), dtype=torch.uint8,
+                     device="cuda")
+    if kind == "wt":
+        wtg.wt_build(t, sigma, ws=ws)
+    else:
+        wtg.wm_build(t, sigma, ws=ws)
+    try:
+        wtg.wt_sync_status(ws)
+        first = 0
+    except wtg.WtError as e:
+        first = e.code
+    wtg.wt_sync_status(ws)                 # cleared after being reported
+    return first
+
+
+@pytest.mark.parametrize("n", [100, 256, 1000, 3000])
+@pytest.mark.parametrize("kind", ["wt", "wm"])
+def test_small_text_symbol_out_of_range_is_reported(kind, n):
+    """Texts of at most 4096 symbols in one round are built by the small-job kernels
+    alone (no histogram pass): they report a symbol >= sigma too."""
+    T = synth.uniform_text(n, 200, 5 + n, np.uint8)
+    assert _status_after_build(kind, T, 200) == 0
+    T[n // 2] = 230
+    assert _status_after_build(kind, T, 200) == 2
+
+
+@pytest.mark.parametrize("kind", ["wt", "wm"])
+def test_small_text_beyond_the_code_bits_is_reported(kind):
+    """A 16-bit stored text over sigma = 16 with a value of 300: beyond the 4 code
+    bits, so out of range, though its low byte would be a valid class."""
+    T = synth.uniform_text(500, 16, 9, np.uint16)
+    T[123] = 300
+    assert _status_after_build(kind, T, 16) == 2
