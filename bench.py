@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the kernel source makes the figure stale, and `traffic` is then reported as null.
 TRAFFIC_CAPTURES = {
     # ncu --set full of k_build_bs, n = 2^28 uint8 WT build (the third k_build_bs launch)
-    "5beba8e2f087c155c1e30a6d005c5f471277becd895731ddd7ef5cf875f0e843": {"dram_bytes": 313189120 + 225406208,
+    "ddd7964e064fdd1b1fd2782f3e087db96d80eb0fdce5aa1db275cbc3efde706e": {"dram_bytes": 313139200 + 225358080,
                                                                          "n": 1 << 28},
 }
 
